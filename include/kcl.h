@@ -1,0 +1,156 @@
+/*
+ * kcl.h — C ABI of the GB300 k-clique listing library (SDegree and BitCol,
+ * with Pre-Core and Pre-List), after "Efficient k-clique Listing with Set
+ * Intersection Speedup".
+ *
+ * Problem (Section III-A, Definition 2): given an undirected simple graph
+ * G(V, E) and an integer k >= 3, find every k-vertex subset whose vertices
+ * are pairwise adjacent.  The library counts them exactly, and in listing
+ * mode also writes each one and returns an order-independent checksum.
+ *
+ * Conventions shared by every call
+ *  - Input graph: symmetric CSR.  row_ptr is uint64[n+1] with row_ptr[0] = 0,
+ *    col is uint32[row_ptr[n]]; every row strictly ascending (so no duplicate
+ *    edges), no self-loops, every id < n, and v in row u iff u in row v.
+ *    Anything else is rejected with KCL_EINVAL and nothing is kept.
+ *  - Pointers are plain host or device addresses; no framework types cross
+ *    this boundary.  `stream` is a cudaStream_t passed as void* (NULL = the
+ *    legacy default stream).  Every call is ordered on the graph's stream and
+ *    returns only when its results are on the host.
+ *  - Ownership: the library copies the input graph into device memory it
+ *    owns (freed by kcl_free_graph).  Output buffers (ring, per-root arrays)
+ *    belong to the caller.
+ *  - Errors never leave the device trapped: device-side checks record a
+ *    status word that the call turns into its return code.
+ *  - Not thread-safe per graph: calls on one kcl_graph must not overlap.
+ *
+ * Checksum: for a clique with ids v_1 < ... < v_k (the caller's original
+ * ids), H = f(... f(f(G ^ k) ^ v_1) ... ^ v_k) with G = 0x9E3779B97F4A7C15
+ * and f the SplitMix64 output finaliser (Steele, Lea & Flood, OOPSLA 2014);
+ * the checksum is the sum of H over all cliques mod 2^64.  The paper defines
+ * no checksum; this one does not depend on listing order or scheduling.
+ */
+#ifndef KCL_H
+#define KCL_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct kcl_graph kcl_graph;
+
+typedef enum {
+    KCL_OK = 0,
+    KCL_EINVAL = 1,     /* bad argument or malformed graph */
+    KCL_ENOMEM = 2,     /* device or host allocation failed */
+    KCL_EOVERFLOW = 3,  /* the exact count does not fit in 64 bits */
+    KCL_ETRUNC = 4,     /* listing: more cliques than ring capacity (wrap = 0) */
+    KCL_ETIMEOUT = 5,   /* a bounded device-side wait gave up */
+    KCL_ECUDA = 6,      /* a CUDA runtime call failed */
+    KCL_EABORT = 7,     /* aborted by the caller */
+    KCL_ELIMIT = 8      /* a built-in size limit was exceeded (see kcl_strerror) */
+} kcl_status;
+
+/* Vertex orderings of the two algorithms.
+ * KCL_ORDER_DEGREE: SDegree (Algorithm 5, Section VI).  Pre-Core, Pre-List,
+ *   then the DAG u -> v iff (d_u, u) < (d_v, v) with degrees of the reduced
+ *   graph, and SDegreeList with sorted-list intersections N+_v and C.
+ * KCL_ORDER_COLOR: BitCol (Algorithm 6, Section VII).  Pre-Core, Pre-List,
+ *   the degeneracy DAG (bulk peel rounds: eta = (round, id)), then for each
+ *   root the subgraph induced by its out-neighbours, greedy colour ordering
+ *   (Section VII-A), bitmap encoding (Section VII-C) and BitColList with
+ *   colour pruning. */
+typedef enum { KCL_ORDER_DEGREE = 0, KCL_ORDER_COLOR = 1 } kcl_ordering;
+
+/* Largest supported k (the paper requires k >= 3, Section III-A). */
+#define KCL_MAX_K 32
+/* Largest supported out-degree of a root in the oriented graph. */
+#define KCL_MAX_OUTDEG 65535
+
+/* Caller-owned device buffer for listed cliques: `capacity` records of k
+ * uint32 ids each, ids sorted ascending within a record; record order is
+ * unspecified.  wrap = 0: writing stops at capacity and the call returns
+ * KCL_ETRUNC (count and checksum still cover every clique).  wrap = 1:
+ * records land at (index mod capacity); the ring keeps an arbitrary subset
+ * and the call returns KCL_OK. */
+typedef struct {
+    uint32_t *ids;
+    uint64_t capacity;
+    int wrap;
+} kcl_ring;
+
+/* Copy a graph in and validate it (Section III-A problem input).
+ * n: vertex count (0 allowed).  row_ptr/col: CSR as above, host memory if
+ * on_device = 0, device memory of the current device if on_device = 1.
+ * stream: cudaStream_t (void*) used for this graph from now on.
+ * out: receives the new graph handle; NULL on error.
+ * Returns KCL_EINVAL for a malformed graph, KCL_ENOMEM, KCL_ECUDA. */
+kcl_status kcl_load_csr(uint32_t n, const uint64_t *row_ptr, const uint32_t *col,
+                        int on_device, void *stream, kcl_graph **out);
+
+/* Release a graph and all device memory it owns.  NULL is ignored. */
+void kcl_free_graph(kcl_graph *g);
+
+/* Change the stream that later calls on g are ordered on. */
+kcl_status kcl_set_stream(kcl_graph *g, void *stream);
+
+uint32_t kcl_num_vertices(const kcl_graph *g);
+uint64_t kcl_num_edges(const kcl_graph *g);   /* undirected edges */
+
+/* Count the k-cliques of g (Algorithms 5 and 6 with Pre-Core and Pre-List,
+ * Sections V-VII).  k in [3, KCL_MAX_K].  *count receives the exact count.
+ * KCL_EOVERFLOW if it exceeds 2^64 - 1; KCL_ELIMIT if a root's out-degree
+ * exceeds KCL_MAX_OUTDEG. */
+kcl_status kcl_count(kcl_graph *g, uint32_t k, kcl_ordering ord, uint64_t *count);
+
+/* List the k-cliques of g into `ring` (device memory, see kcl_ring) and
+ * return the exact count, the checksum and the number of records written
+ * (min(count, capacity) without wrap; min(count, capacity) with wrap too).
+ * The output lines of Algorithms 4, 5 and 6: each clique once, as its
+ * original ids sorted ascending. */
+kcl_status kcl_list(kcl_graph *g, uint32_t k, kcl_ordering ord, const kcl_ring *ring,
+                    uint64_t *count, uint64_t *checksum, uint64_t *written);
+
+/* Per-root counts, for checking against an independent implementation.
+ * per_root: device uint64[n], overwritten with the number of k-cliques whose
+ * lowest vertex in the ordering eta is that vertex (Theorem 1: each clique is
+ * found once, from its eta-first vertex).  Cliques reported by Pre-List are
+ * not attributed to a root; *prelist_count receives their number and
+ * *count the total. */
+kcl_status kcl_count_per_root(kcl_graph *g, uint32_t k, kcl_ordering ord, uint64_t *per_root,
+                              uint64_t *count, uint64_t *prelist_count);
+
+/* Intermediate results of the front end, for stage-by-stage checks.
+ * Any pointer may be NULL.  Host buffers of n elements:
+ *   alive_core:  1 iff the vertex survives Pre-Core (the (k-1)-core, Alg. 3)
+ *   alive_final: 1 iff it also survives Pre-List (Algorithm 4)
+ *   outdeg:      out-degree in the DAG of `ord` (0 for removed vertices)
+ *   key:         ordering key (reduced degree, or degeneracy peel round)
+ * prelist_count: k-cliques reported by Pre-List; max_outdeg: Delta. */
+kcl_status kcl_stage_info(kcl_graph *g, uint32_t k, kcl_ordering ord, uint8_t *alive_core,
+                          uint8_t *alive_final, uint32_t *outdeg, uint32_t *key,
+                          uint64_t *prelist_count, uint32_t *max_outdeg);
+
+/* Device time of the stages of the last kcl_count / kcl_list call on g, in
+ * milliseconds, measured with CUDA events on the graph's stream when timing
+ * is enabled (kcl_enable_timing).  stage ids: 0 Pre-Core, 1 Pre-List,
+ * 2 orientation, 3 listing kernels (SDegreeList / subgraph build + BitColList),
+ * 4 whole call.  launches[i] = kernel launches in stage i. */
+#define KCL_NUM_STAGES 5
+typedef struct {
+    float ms[KCL_NUM_STAGES];
+    uint32_t launches[KCL_NUM_STAGES];
+} kcl_timing;
+kcl_status kcl_enable_timing(kcl_graph *g, int enable);
+kcl_status kcl_last_timing(const kcl_graph *g, kcl_timing *t);
+
+/* Human-readable text for a status. */
+const char *kcl_strerror(kcl_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* KCL_H */

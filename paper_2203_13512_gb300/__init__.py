@@ -1,0 +1,251 @@
+"""GB300 k-clique listing (SDegree / BitCol with Pre-Core and Pre-List).
+
+Thin Python binding of the C ABI in ``include/kcl.h``: every function here has
+the name of the C entry point it calls and only marshals arguments (numpy
+arrays or torch tensors in, plain pointers and sizes out).  All work runs in
+the CUDA library ``libkcl.so``; there is no CPU fallback, and importing this
+package fails loudly if the library has not been built
+(``python -c "import __graft_entry__ as g; g.build()"``).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libkcl.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(
+        "libkcl.so is missing: build the CUDA library first "
+        "(python -c 'import __graft_entry__ as g; g.build()')")
+
+_lib = ctypes.CDLL(LIB_PATH)
+
+KCL_OK, KCL_EINVAL, KCL_ENOMEM, KCL_EOVERFLOW, KCL_ETRUNC = 0, 1, 2, 3, 4
+KCL_ETIMEOUT, KCL_ECUDA, KCL_EABORT, KCL_ELIMIT = 5, 6, 7, 8
+KCL_ORDER_DEGREE, KCL_ORDER_COLOR = 0, 1
+KCL_MAX_K = 32
+KCL_NUM_STAGES = 5
+STAGES = ("pre_core", "pre_list", "orientation", "listing", "total")
+ORDERINGS = {"degree": KCL_ORDER_DEGREE, "color": KCL_ORDER_COLOR,
+             "sdegree": KCL_ORDER_DEGREE, "bitcol": KCL_ORDER_COLOR}
+
+
+class KclError(RuntimeError):
+    def __init__(self, status, what):
+        msg = _lib.kcl_strerror(status).decode()
+        super().__init__("%s: %s (status %d)" % (what, msg, status))
+        self.status = status
+
+
+class _Ring(ctypes.Structure):
+    _fields_ = [("ids", ctypes.c_void_p), ("capacity", ctypes.c_uint64), ("wrap", ctypes.c_int)]
+
+
+class _Timing(ctypes.Structure):
+    _fields_ = [("ms", ctypes.c_float * KCL_NUM_STAGES),
+                ("launches", ctypes.c_uint32 * KCL_NUM_STAGES)]
+
+
+_P, _U32, _U64, _I = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int
+_sig = {
+    "kcl_load_csr": ([_U32, _P, _P, _I, _P, ctypes.POINTER(_P)], _I),
+    "kcl_free_graph": ([_P], None),
+    "kcl_set_stream": ([_P, _P], _I),
+    "kcl_num_vertices": ([_P], _U32),
+    "kcl_num_edges": ([_P], _U64),
+    "kcl_count": ([_P, _U32, _I, ctypes.POINTER(_U64)], _I),
+    "kcl_list": ([_P, _U32, _I, ctypes.POINTER(_Ring), ctypes.POINTER(_U64),
+                  ctypes.POINTER(_U64), ctypes.POINTER(_U64)], _I),
+    "kcl_count_per_root": ([_P, _U32, _I, _P, ctypes.POINTER(_U64), ctypes.POINTER(_U64)], _I),
+    "kcl_stage_info": ([_P, _U32, _I, _P, _P, _P, _P, ctypes.POINTER(_U64),
+                        ctypes.POINTER(_U32)], _I),
+    "kcl_enable_timing": ([_P, _I], _I),
+    "kcl_last_timing": ([_P, ctypes.POINTER(_Timing)], _I),
+    "kcl_strerror": ([_I], ctypes.c_char_p),
+}
+for _name, (_args, _res) in _sig.items():
+    _f = getattr(_lib, _name)
+    _f.argtypes = _args
+    _f.restype = _res
+
+
+def _ord(ordering):
+    if isinstance(ordering, str):
+        return ORDERINGS[ordering.lower()]
+    return int(ordering)
+
+
+def _check(st, what, ok=(KCL_OK,)):
+    if st not in ok:
+        raise KclError(st, what)
+    return st
+
+
+def _current_stream():
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    except ImportError:
+        pass
+    return ctypes.c_void_p(0)
+
+
+def _dev_ptr(t, dtype_name, numel=None):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("expected a CUDA tensor")
+    if str(t.dtype) != "torch." + dtype_name:
+        raise TypeError("expected dtype %s, got %s" % (dtype_name, t.dtype))
+    if not t.is_contiguous():
+        raise TypeError("expected a contiguous tensor")
+    if numel is not None and t.numel() < numel:
+        raise ValueError("tensor too small: %d < %d" % (t.numel(), numel))
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Graph:
+    """Owning handle of a device-resident graph (``kcl_graph*``)."""
+
+    def __init__(self, handle, n, m):
+        self._h = handle
+        self.n = n
+        self.m = m
+
+    @property
+    def handle(self):
+        if self._h is None:
+            raise ValueError("graph already freed")
+        return self._h
+
+    def free(self):
+        if self._h is not None:
+            _lib.kcl_free_graph(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def kcl_load_csr(row_ptr, col, stream=None):
+    """Copy a symmetric CSR graph into the library (validated on the device).
+
+    ``row_ptr``/``col`` are numpy arrays (host) or CUDA tensors (device),
+    dtypes uint64/uint32 (torch: int64/int32 reinterpreted)."""
+    try:
+        import torch
+        on_dev = isinstance(row_ptr, torch.Tensor) and row_ptr.is_cuda
+    except ImportError:
+        on_dev = False
+    if on_dev:
+        # device CSR: int64 row offsets and int32 ids, bit-identical to the
+        # uint64 / uint32 layout of the C ABI
+        n = row_ptr.numel() - 1
+        rp_p = _dev_ptr(row_ptr, "int64")
+        c_p = _dev_ptr(col, "int32") if col.numel() else None
+        keep = (row_ptr, col)
+    else:
+        rp = np.ascontiguousarray(row_ptr, dtype=np.uint64)
+        c = np.ascontiguousarray(col, dtype=np.uint32)
+        n = len(rp) - 1
+        rp_p = ctypes.c_void_p(rp.ctypes.data)
+        c_p = ctypes.c_void_p(c.ctypes.data) if c.size else None
+        keep = (rp, c)
+    h = ctypes.c_void_p()
+    s = stream if stream is not None else _current_stream()
+    st = _lib.kcl_load_csr(n, rp_p, c_p, 1 if on_dev else 0, s, ctypes.byref(h))
+    del keep
+    _check(st, "kcl_load_csr")
+    return Graph(h, n, int(_lib.kcl_num_edges(h)))
+
+
+def kcl_free_graph(g):
+    g.free()
+
+
+def kcl_set_stream(g, stream=None):
+    _check(_lib.kcl_set_stream(g.handle, stream if stream is not None else _current_stream()),
+           "kcl_set_stream")
+
+
+def kcl_count(g, k, ordering="color"):
+    """Exact number of k-cliques (Algorithms 5 / 6)."""
+    c = ctypes.c_uint64()
+    _check(_lib.kcl_count(g.handle, k, _ord(ordering), ctypes.byref(c)), "kcl_count")
+    return int(c.value)
+
+
+def kcl_list(g, k, ordering="color", ring=None, wrap=False):
+    """List the k-cliques into ``ring`` (CUDA int32/uint32 tensor of
+    capacity*k entries, or None for checksum only).  Returns
+    (count, checksum, written, truncated)."""
+    r = _Ring()
+    if ring is not None:
+        if ring.numel() % k:
+            raise ValueError("ring size must be a multiple of k")
+        r.ids = ctypes.c_void_p(ring.data_ptr())
+        r.capacity = ring.numel() // k
+        r.wrap = 1 if wrap else 0
+    c, s, w = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64()
+    st = _lib.kcl_list(g.handle, k, _ord(ordering), ctypes.byref(r), ctypes.byref(c),
+                       ctypes.byref(s), ctypes.byref(w))
+    _check(st, "kcl_list", ok=(KCL_OK, KCL_ETRUNC))
+    return int(c.value), int(s.value), int(w.value), st == KCL_ETRUNC
+
+
+def kcl_count_per_root(g, k, ordering, per_root):
+    """Fill ``per_root`` (CUDA int64 tensor, n entries) with per-root counts;
+    returns (total, prelist_count)."""
+    c, p = ctypes.c_uint64(), ctypes.c_uint64()
+    ptr = ctypes.c_void_p(per_root.data_ptr())
+    if per_root.numel() < g.n:
+        raise ValueError("per_root too small")
+    _check(_lib.kcl_count_per_root(g.handle, k, _ord(ordering), ptr, ctypes.byref(c),
+                                   ctypes.byref(p)), "kcl_count_per_root")
+    return int(c.value), int(p.value)
+
+
+def kcl_stage_info(g, k, ordering):
+    """Front-end intermediates as numpy arrays: alive_core, alive_final,
+    outdeg, key, prelist_count, max_outdeg."""
+    n = g.n
+    ac = np.zeros(max(n, 1), np.uint8)
+    af = np.zeros(max(n, 1), np.uint8)
+    od = np.zeros(max(n, 1), np.uint32)
+    ky = np.zeros(max(n, 1), np.uint32)
+    pc, mo = ctypes.c_uint64(), ctypes.c_uint32()
+    _check(_lib.kcl_stage_info(g.handle, k, _ord(ordering), ac.ctypes.data, af.ctypes.data,
+                               od.ctypes.data, ky.ctypes.data, ctypes.byref(pc), ctypes.byref(mo)),
+           "kcl_stage_info")
+    return {"alive_core": ac[:n], "alive_final": af[:n], "outdeg": od[:n], "key": ky[:n],
+            "prelist_count": int(pc.value), "max_outdeg": int(mo.value)}
+
+
+def kcl_enable_timing(g, enable=True):
+    _check(_lib.kcl_enable_timing(g.handle, 1 if enable else 0), "kcl_enable_timing")
+
+
+def kcl_last_timing(g):
+    t = _Timing()
+    _check(_lib.kcl_last_timing(g.handle, ctypes.byref(t)), "kcl_last_timing")
+    return ({STAGES[i]: float(t.ms[i]) for i in range(KCL_NUM_STAGES)},
+            {STAGES[i]: int(t.launches[i]) for i in range(KCL_NUM_STAGES)})
+
+
+def kcl_strerror(status):
+    return _lib.kcl_strerror(status).decode()
+
+
+def kcl_num_vertices(g):
+    return int(_lib.kcl_num_vertices(g.handle))
+
+
+def kcl_num_edges(g):
+    return int(_lib.kcl_num_edges(g.handle))

@@ -1,0 +1,160 @@
+// Internal declarations shared by the library's CUDA translation units.
+// Not part of the public ABI (include/kcl.h is).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/kcl.h"
+
+namespace kcl {
+
+constexpr int kWarp = 32;
+
+// Device status word bits (recorded by kernels, turned into a kcl_status).
+enum : uint32_t {
+    DEV_ERR_NONE = 0,
+    DEV_ERR_INVALID_GRAPH = 1u << 0,
+    DEV_ERR_OUTDEG_LIMIT = 1u << 1,
+    DEV_ERR_OVERFLOW = 1u << 2,
+    DEV_ERR_INTERNAL = 1u << 3,
+};
+
+// Result words written by the device and read back once per call.
+struct DevResult {
+    unsigned long long count;        // k-cliques found by the listing kernels
+    unsigned long long checksum;     // sum of clique hashes (list mode)
+    unsigned long long emitted;      // clique records claimed in the ring
+    unsigned long long pre_count;    // k-cliques of Pre-List clique components
+    unsigned long long pre_checksum;
+    unsigned long long count_carry;  // set when an addition to `count` wrapped
+    unsigned int status;             // DEV_ERR_* bits
+    unsigned int frontier;           // size of the next peel frontier
+    unsigned int max_outdeg;         // Delta of the DAG
+    unsigned int n_roots;            // roots with d+ >= k-1
+    unsigned int min_deg;            // minimum current degree (degeneracy peel)
+    unsigned int remaining;          // vertices not yet peeled
+    unsigned int n_clique_comps;     // components removed by Pre-List
+    unsigned int pad;
+};
+
+// Workspace owned by a graph, grown on demand and reused across calls.
+struct Workspace {
+    uint8_t *alive = nullptr;        // n
+    uint8_t *alive_core = nullptr;   // n (copy after Pre-Core, for stage info)
+    uint32_t *cdeg = nullptr;        // n: current degree in the alive subgraph
+    uint32_t *key = nullptr;         // n: ordering key (degree or peel round)
+    uint32_t *peel_deg = nullptr;    // n: degrees during the degeneracy peel
+    uint32_t *frontier_a = nullptr;  // n
+    uint32_t *frontier_b = nullptr;  // n
+    uint32_t *parent = nullptr;      // n: union-find forest (Pre-List)
+    uint32_t *comp_n = nullptr;      // n: component sizes (by root)
+    unsigned long long *comp_sdeg = nullptr;  // n: component degree sums
+    uint32_t *comp_flag = nullptr;   // n: 1 = clique component root
+    uint32_t *outdeg = nullptr;      // n
+    uint32_t *optr = nullptr;        // n + 1: out-CSR offsets
+    uint32_t *oadj = nullptr;        // nnz/2: out-neighbours, ascending id
+    uint32_t *roots = nullptr;       // n: roots sorted by d+ descending
+    uint32_t *hist = nullptr;        // histogram / scan scratch
+    uint32_t *scan_tmp = nullptr;    // block sums for scans
+    unsigned int *queue = nullptr;   // per-class work counters
+    uint32_t *members = nullptr;     // n: clique-component members (listing)
+    uint32_t *comp_slot = nullptr;   // n: clique-component slot (listing)
+    uint32_t *arena = nullptr;       // global scratch for large subproblems
+    size_t arena_words = 0;
+    DevResult *res = nullptr;
+    DevResult *h_res = nullptr;      // pinned host mirror
+    uint32_t n_cap = 0;
+    uint64_t nnz_cap = 0;
+};
+
+struct Timing {
+    int enabled = 0;
+    cudaEvent_t ev[2 * KCL_NUM_STAGES] = {};
+    float ms[KCL_NUM_STAGES] = {};
+    uint32_t launches[KCL_NUM_STAGES] = {};
+};
+
+}  // namespace kcl
+
+struct kcl_graph {
+    uint32_t n = 0;
+    uint64_t nnz = 0;          // directed entries = 2 |E|
+    int device = 0;
+    int num_sms = 0;
+    cudaStream_t stream = nullptr;
+    uint64_t *rp = nullptr;    // device CSR
+    uint32_t *col = nullptr;
+    uint32_t max_deg = 0;
+    kcl::Workspace ws;
+    kcl::Timing timing;
+};
+
+namespace kcl {
+
+// ------------------------------------------------------------ utilities
+__device__ __forceinline__ uint64_t mix64(uint64_t z) {
+    // SplitMix64 output finaliser (Steele, Lea & Flood 2014)
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+__device__ __forceinline__ uint64_t hash_seed(uint32_t k) {
+    return mix64(0x9E3779B97F4A7C15ull ^ (uint64_t)k);
+}
+
+__device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
+
+// Add to a 64-bit counter and flag a wrap-around in `carry`.
+__device__ __forceinline__ void add_count(unsigned long long *dst, unsigned long long *carry,
+                                          unsigned long long x) {
+    if (x == 0) return;
+    unsigned long long old = atomicAdd(dst, x);
+    if (old + x < old) atomicExch(carry, 1ull);
+}
+
+// ------------------------------------------------------ host-side launchers
+// Every launcher enqueues on `s` and returns the number of kernel launches.
+
+// kcl_prep.cu
+int launch_validate(const kcl_graph *g, DevResult *res, cudaStream_t s);
+int launch_degrees(const kcl_graph *g, uint32_t *deg, cudaStream_t s);
+int launch_precore_init(const kcl_graph *g, uint32_t k, Workspace &w, cudaStream_t s);
+int launch_precore_round(const kcl_graph *g, uint32_t k, const uint32_t *fin, uint32_t nin,
+                         uint32_t *fout, Workspace &w, cudaStream_t s);
+int launch_prelist(const kcl_graph *g, uint32_t k, Workspace &w, int listing, cudaStream_t s);
+int launch_prelist_emit(const kcl_graph *g, uint32_t k, Workspace &w, uint32_t n_comps,
+                        const kcl_ring *ring, cudaStream_t s);
+int launch_degree_key(const kcl_graph *g, Workspace &w, cudaStream_t s);
+int launch_peel_init(const kcl_graph *g, Workspace &w, cudaStream_t s);
+int launch_peel_select_all(const kcl_graph *g, Workspace &w, uint32_t t, uint32_t round,
+                           uint32_t *fout, cudaStream_t s);
+int launch_peel_update(const kcl_graph *g, Workspace &w, const uint32_t *fin, uint32_t nin,
+                       uint32_t t, uint32_t round, uint32_t *fout, cudaStream_t s);
+int launch_peel_min(const kcl_graph *g, Workspace &w, cudaStream_t s);
+int launch_orient(const kcl_graph *g, uint32_t k, Workspace &w, cudaStream_t s);
+int launch_roots(const kcl_graph *g, uint32_t k, Workspace &w, uint32_t max_outdeg,
+                 uint32_t *class_begin, const uint32_t *class_limits, int n_classes,
+                 cudaStream_t s);
+int launch_exclusive_scan(const uint32_t *in, uint32_t *out, uint32_t n, uint32_t *block_tmp,
+                          cudaStream_t s);
+
+// kcl_bitcol.cu
+struct ListArgs {
+    uint32_t *ring = nullptr;
+    unsigned long long capacity = 0;
+    int wrap = 0;
+    int listing = 0;
+    unsigned long long *per_root = nullptr;
+};
+int bitcol_classes(uint32_t *limits, int max);
+int launch_bitcol(const kcl_graph *g, uint32_t k, Workspace &w, const uint32_t *class_begin,
+                  int n_classes, const ListArgs &la, cudaStream_t s);
+
+// kcl_sdegree.cu
+int sdegree_classes(uint32_t *limits, int max);
+int launch_sdegree(const kcl_graph *g, uint32_t k, Workspace &w, const uint32_t *class_begin,
+                   int n_classes, const ListArgs &la, cudaStream_t s);
+
+}  // namespace kcl

@@ -1,0 +1,225 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Counts, checksums, listed cliques, per-root counts and the front-end stages
+must match exactly: the whole computation is integer work.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import kclgen
+import oracle
+from tests.graphs import complete, csr_from_edges, gnp
+
+pytestmark = pytest.mark.gpu
+
+ORDS = ("degree", "color")
+
+
+@pytest.fixture(scope="module")
+def kcl():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    import paper_2203_13512_gb300 as kcl
+    return kcl
+
+
+def _ring(kcl, k, cap):
+    import torch
+    return torch.zeros(cap * k, dtype=torch.int32, device="cuda")
+
+
+def _listed(ring, k, written):
+    a = ring[: written * k].cpu().numpy().astype(np.uint32).reshape(-1, k)
+    return sorted(tuple(int(x) for x in r) for r in a)
+
+
+def _oracle_mode(ordering):
+    return oracle.sdegree if ordering == "degree" else oracle.bitcol
+
+
+# ------------------------------------------------------------ worked example
+@pytest.mark.parametrize("ordering", ORDS)
+def test_worked_example_counts_and_listing(kcl, fig1, ordering):
+    rp, col = fig1
+    g = kcl.kcl_load_csr(rp, col)
+    for k in (3, 4, 5, 6):
+        ref_c, ref_s, ref_l = oracle.plain(rp, col, k, list_cap=1000)
+        assert kcl.kcl_count(g, k, ordering) == ref_c
+        ring = _ring(kcl, k, 1000)
+        c, s, w, trunc = kcl.kcl_list(g, k, ordering, ring)
+        assert (c, s, w, trunc) == (ref_c, ref_s, ref_c, False)
+        assert _listed(ring, k, w) == sorted(tuple(int(x) for x in r) for r in ref_l)
+    # Example 1: the three 4-cliques
+    ring = _ring(kcl, 4, 8)
+    c, s, w, _ = kcl.kcl_list(g, 4, ordering, ring)
+    assert _listed(ring, 4, w) == [(1, 2, 3, 4), (1, 2, 4, 6), (9, 10, 11, 12)]
+
+
+def test_worked_example_stages(kcl, fig1):
+    rp, col = fig1
+    g = kcl.kcl_load_csr(rp, col)
+    k = 4
+    core = oracle.precore(rp, col, k)
+    pl = oracle.prelist(rp, col, k, core)
+    for ordering, mode in (("degree", 0), ("color", 1)):
+        st = kcl.kcl_stage_info(g, k, ordering)
+        assert np.array_equal(st["alive_core"], core)          # Example 2
+        assert np.array_equal(st["alive_final"], pl["alive"])  # Example 3
+        assert st["prelist_count"] == pl["count"] == 1
+        assert np.array_equal(st["outdeg"], oracle.outdegrees(rp, col, pl["alive"], mode))
+    # Example 4's DAG: d+ = v1:0 v2:4 v3:2 v4:2 v5:3 v6:1
+    st = kcl.kcl_stage_info(g, k, "degree")
+    assert [int(st["outdeg"][v]) for v in range(1, 7)] == [0, 4, 2, 2, 3, 1]
+    st = kcl.kcl_stage_info(g, k, "color")
+    rounds, _ = oracle.degeneracy_rounds(rp, col, pl["alive"])
+    assert np.array_equal(st["key"], rounds)
+
+
+# ----------------------------------------------------------- random graphs
+@pytest.mark.parametrize("seed", range(10))
+def test_random_small_graphs(kcl, seed):
+    rng = np.random.default_rng(300 + seed)
+    n = int(rng.integers(5, 41))
+    p = float(rng.choice([0.15, 0.35, 0.55, 0.75, 0.9]))
+    rp, col = gnp(n, p, 500 + seed)
+    g = kcl.kcl_load_csr(rp, col)
+    for k in range(3, 9):
+        ref = oracle.plain(rp, col, k)
+        for ordering in ORDS:
+            c, s, _, _ = kcl.kcl_list(g, k, ordering, None)
+            assert (c, s) == ref, (k, ordering)
+            assert kcl.kcl_count(g, k, ordering) == ref[0]
+
+
+# ----------------------------------------------- small Chung-Lu workload
+@pytest.fixture(scope="module")
+def small_workload():
+    return kclgen.chung_lu_planted_small(seed=1)
+
+
+@pytest.mark.parametrize("ordering", ORDS)
+def test_small_workload_counts_checksums_per_root(kcl, small_workload, ordering):
+    import torch
+    rp, col = small_workload
+    g = kcl.kcl_load_csr(rp, col)
+    n = len(rp) - 1
+    for k in range(3, 10):
+        ref_c, ref_s = oracle.plain(rp, col, k)
+        assert kcl.kcl_count(g, k, ordering) == ref_c
+        c, s, _, _ = kcl.kcl_list(g, k, ordering, None)
+        assert (c, s) == (ref_c, ref_s)
+        pr = torch.zeros(n, dtype=torch.int64, device="cuda")
+        tot, pre = kcl.kcl_count_per_root(g, k, ordering, pr)
+        o = _oracle_mode(ordering)(rp, col, k, per_root=True)
+        assert tot == ref_c
+        assert np.array_equal(pr.cpu().numpy().astype(np.uint64), o["per_root"])
+
+
+@pytest.mark.parametrize("ordering", ORDS)
+def test_small_workload_listing_is_the_clique_set(kcl, small_workload, ordering):
+    rp, col = small_workload
+    g = kcl.kcl_load_csr(rp, col)
+    for k in (5, 7):
+        ref_c, ref_s, ref_l = oracle.plain(rp, col, k, list_cap=200000)
+        ring = _ring(kcl, k, ref_c + 5)
+        c, s, w, trunc = kcl.kcl_list(g, k, ordering, ring)
+        assert (c, s, w, trunc) == (ref_c, ref_s, ref_c, False)
+        assert _listed(ring, k, w) == sorted(tuple(int(x) for x in r) for r in ref_l)
+
+
+# ------------------------------------------------ every out-degree class
+@pytest.mark.parametrize("size,p", [(40, 0.9), (70, 0.8), (110, 0.7), (170, 0.6), (260, 0.45)])
+def test_planted_communities_span_the_classes(kcl, size, p):
+    rp, col = kclgen.chung_lu(3000, 12000, 2.3, groups=3, group_size=(size, size), group_p=p,
+                              seed=size)
+    g = kcl.kcl_load_csr(rp, col)
+    for k in (3, 4, 5):
+        ref = oracle.plain(rp, col, k)
+        for ordering in ORDS:
+            c, s, _, _ = kcl.kcl_list(g, k, ordering, None)
+            assert (c, s) == ref, (k, ordering)
+
+
+def _near_complete(n):
+    """K_n minus the edge {0, 1}: C(n,k) - C(n-2,k-2) k-cliques, and no
+    Pre-List shortcut (the component is not a clique)."""
+    return csr_from_edges(n, [(u, v) for u in range(n) for v in range(u + 1, n) if (u, v) != (0, 1)])
+
+
+@pytest.mark.parametrize("n", [300, 700, 1300])
+def test_large_outdegree_arena_classes(kcl, n):
+    rp, col = _near_complete(n)
+    g = kcl.kcl_load_csr(rp, col)
+    for k in (3, 4):
+        want = math.comb(n, k) - math.comb(n - 2, k - 2)
+        res = {o: kcl.kcl_list(g, k, o, None)[:2] for o in ORDS}
+        assert res["degree"][0] == want and res["color"][0] == want
+        assert res["degree"][1] == res["color"][1]
+    if n == 300:
+        assert kcl.kcl_list(g, 3, "color", None)[:2] == oracle.plain(rp, col, 3)
+
+
+# ------------------------------------------------------------- edge cases
+def test_edge_cases(kcl):
+    # empty graph, no edges, single edge
+    for n, edges in ((0, []), (5, []), (2, [(0, 1)])):
+        rp, col = csr_from_edges(n, edges)
+        g = kcl.kcl_load_csr(rp, col)
+        for o in ORDS:
+            assert kcl.kcl_count(g, 3, o) == 0
+            assert kcl.kcl_list(g, 3, o, None)[:3] == (0, 0, 0)
+    # K_k alone: Pre-List reports it; K_n with n < k: nothing
+    for n, k in ((3, 3), (8, 8), (12, 5), (6, 9), (33, 32)):
+        rp, col = complete(n)
+        g = kcl.kcl_load_csr(rp, col)
+        ref = oracle.plain(rp, col, k)
+        for o in ORDS:
+            assert kcl.kcl_list(g, k, o, None)[:2] == ref
+    # k bounds
+    rp, col = complete(5)
+    g = kcl.kcl_load_csr(rp, col)
+    for bad_k in (0, 1, 2, 33):
+        with pytest.raises(kcl.KclError) as e:
+            kcl.kcl_count(g, bad_k, "color")
+        assert e.value.status == kcl.KCL_EINVAL
+
+
+def test_malformed_graphs_rejected(kcl):
+    bad = [
+        (np.array([0, 1, 1], np.uint64), np.array([1], np.uint32)),              # asymmetric
+        (np.array([0, 1, 2], np.uint64), np.array([0, 1], np.uint32)),           # self-loops
+        (np.array([0, 2, 4], np.uint64), np.array([1, 1, 0, 0], np.uint32)),     # duplicates
+        (np.array([0, 2, 3, 4], np.uint64), np.array([2, 1, 0, 0], np.uint32)),  # unsorted
+        (np.array([0, 1, 2], np.uint64), np.array([5, 0], np.uint32)),           # out of range
+        (np.array([1, 1, 2], np.uint64), np.array([1, 0], np.uint32)),           # row_ptr[0] != 0
+    ]
+    for rp, col in bad:
+        with pytest.raises(kcl.KclError) as e:
+            kcl.kcl_load_csr(rp, col)
+        assert e.value.status == kcl.KCL_EINVAL
+
+
+def test_ring_truncation_and_wrap(kcl, small_workload):
+    rp, col = small_workload
+    g = kcl.kcl_load_csr(rp, col)
+    k = 5
+    ref_c, ref_s = oracle.plain(rp, col, k)
+    for o in ORDS:
+        ring = _ring(kcl, k, 1000)
+        c, s, w, trunc = kcl.kcl_list(g, k, o, ring, wrap=False)
+        assert (c, s, w, trunc) == (ref_c, ref_s, 1000, True)
+        got = _listed(ring, k, w)
+        assert len(set(got)) == 1000
+        ring = _ring(kcl, k, 777)
+        c, s, w, trunc = kcl.kcl_list(g, k, o, ring, wrap=True)
+        assert (c, s, w, trunc) == (ref_c, ref_s, 777, False)
+
+
+def test_device_resident_input(kcl, small_workload):
+    import torch
+    rp, col = small_workload
+    g = kcl.kcl_load_csr(torch.from_numpy(rp.astype(np.int64)).cuda(),
+                         torch.from_numpy(col.astype(np.int32)).cuda())
+    assert kcl.kcl_count(g, 5, "color") == oracle.plain(rp, col, 5)[0]
