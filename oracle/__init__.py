@@ -77,9 +77,9 @@ def _load():
             "oracle_degeneracy_rounds": ([_U32, _P, _P, _P, _P, _P], ctypes.c_int),
             "oracle_outdegrees": ([_U32, _P, _P, _P, ctypes.c_int, _P], ctypes.c_int),
             "oracle_sdegree": ([_U32, _P, _P, _U32, ctypes.c_int, _P, _U32, _P, _P, _P, _P,
-                                _P, _U64, _P, _P, _U64, _P], ctypes.c_int),
+                                _P, _U64, _P, _P, _U64, _P, ctypes.c_int], ctypes.c_int),
             "oracle_bitcol": ([_U32, _P, _P, _U32, ctypes.c_int, _U32, _P, _U32, _P, _P, _P,
-                               _P, _P, _U64, _P], ctypes.c_int),
+                               _P, _P, _U64, _P, ctypes.c_int], ctypes.c_int),
             "oracle_colour_graph": ([_U32, _P, _P, _P, _P], ctypes.c_int),
             "oracle_bitencode_graph": ([_U32, _P, _P, _U32, _P, _P], ctypes.c_int),
         }
@@ -201,7 +201,7 @@ def _roots_arg(roots):
 
 
 def sdegree(row_ptr, col, k, preprocess=True, roots=None, per_root=False, list_cap=0,
-            trace_cap=0):
+            trace_cap=0, count_only=False):
     """Algorithm 5.  Returns dict(count, checksum, counters[, per_root,
     cliques, trace]).  With ``roots`` only those roots are expanded and the
     Pre-List cliques are not included."""
@@ -215,7 +215,7 @@ def sdegree(row_ptr, col, k, preprocess=True, roots=None, per_root=False, list_c
     rc = _load().oracle_sdegree(n, _ptr(rp), _ptr(c), k, 1 if preprocess else 0, _ptr(r), nr,
                                 ctypes.byref(cnt), ctypes.byref(cks), _ptr(pr), ctypes.byref(ctr),
                                 _ptr(out), list_cap, ctypes.byref(wr), _ptr(tr), trace_cap,
-                                ctypes.byref(tl))
+                                ctypes.byref(tl), 1 if count_only else 0)
     _check(rc, "oracle_sdegree", allow_trunc=True)
     res = {"count": int(cnt.value), "checksum": int(cks.value), "counters": ctr.as_dict()}
     if per_root:
@@ -239,7 +239,8 @@ def _parse_trace(t):
     return calls
 
 
-def bitcol(row_ptr, col, k, preprocess=True, L=24, roots=None, per_root=False, list_cap=0):
+def bitcol(row_ptr, col, k, preprocess=True, L=24, roots=None, per_root=False, list_cap=0,
+           count_only=False):
     """Algorithm 6 with an L-bit bitmap word (the paper fixes L = 24)."""
     n, rp, c = _csr(row_ptr, col)
     r, nr = _roots_arg(roots)
@@ -249,7 +250,7 @@ def bitcol(row_ptr, col, k, preprocess=True, L=24, roots=None, per_root=False, l
     out = np.zeros(max(list_cap, 1) * k, dtype=np.uint32) if list_cap else None
     rc = _load().oracle_bitcol(n, _ptr(rp), _ptr(c), k, 1 if preprocess else 0, L, _ptr(r), nr,
                                ctypes.byref(cnt), ctypes.byref(cks), _ptr(pr), ctypes.byref(ctr),
-                               _ptr(out), list_cap, ctypes.byref(wr))
+                               _ptr(out), list_cap, ctypes.byref(wr), 1 if count_only else 0)
     _check(rc, "oracle_bitcol", allow_trunc=True)
     res = {"count": int(cnt.value), "checksum": int(cks.value), "counters": ctr.as_dict()}
     if per_root:

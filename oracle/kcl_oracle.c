@@ -28,6 +28,9 @@
  *   oracle_bitcol   Algorithm 6 (BitCol): degeneracy DAG, per-root colour
  *                   ordering (Section VII-A), BitEncode with an L-bit word
  *                   (Section VII-C), BitColList and BitJoin.
+ *   count_only      (SDegree and BitCol) the same recursion and counters, but
+ *                   the last level adds |C'| instead of enumerating each
+ *                   clique; used to count algorithmic work on large inputs.
  *
  * Readings taken where the paper is silent or inconsistent (each is listed
  * in the design notes):
@@ -75,7 +78,7 @@ typedef struct {
     uint64_t intersections;  /* merge joins (SDegree) or BitJoin calls (BitCol) */
     uint64_t merge_elems;    /* SDegree: sum of (|C| + d+_v) per merge join (Lemma 2) */
     uint64_t bitjoin_words;  /* BitCol: words touched by BitJoin */
-    uint64_t build_reads;    /* BitCol: sum over v in N+_u of d_v (G_u construction) */
+    uint64_t build_reads;    /* BitCol: sum over v in N+_u of d+_v (G_u construction) */
     uint64_t roots;          /* roots with d+_u >= k-1 that were expanded */
     uint64_t max_outdeg;     /* maximum out-degree of the DAG (Delta) */
 } oracle_counters;
@@ -91,8 +94,15 @@ typedef struct {
     uint64_t cap, written;
     uint64_t *per_root;     /* indexed by the root vertex, or NULL */
     uint32_t root;
+    int count_only;         /* count without enumerating (no checksum, no output) */
     uint32_t tmp[64];
 } sink;
+
+/* Count-only mode: add c cliques found at once (the leaf of a recursion). */
+static void sink_add(sink *s, uint64_t c) {
+    s->count += c;
+    if (s->per_root) s->per_root[s->root] += c;
+}
 
 static void sink_emit(sink *s, const uint32_t *ids) {
     uint32_t k = s->k;
@@ -523,7 +533,9 @@ static void sdegree_list(sdeg_ctx *c, uint32_t l, uint32_t nR, const uint32_t *C
         c->cnt->merge_elems += (uint64_t)nC + du;
         if (l == 2) {
             c->R[nR] = u;
-            for (uint32_t j = 0; j < np; j++) { c->R[nR + 1] = Cp[j]; sink_emit(c->S, c->R); }
+            if (c->S->count_only) sink_add(c->S, np);
+            else
+                for (uint32_t j = 0; j < np; j++) { c->R[nR + 1] = Cp[j]; sink_emit(c->S, c->R); }
         } else if (np > l - 2) {
             c->R[nR] = u;
             sdegree_list(c, l - 1, nR + 1, Cp, np);
@@ -535,7 +547,7 @@ int oracle_sdegree(uint32_t n, const uint64_t *rp, const uint32_t *col, uint32_t
                    const uint32_t *roots, uint32_t nroots,
                    uint64_t *count, uint64_t *checksum, uint64_t *per_root,
                    oracle_counters *counters, uint32_t *out, uint64_t cap, uint64_t *written,
-                   uint32_t *trace, uint64_t trace_cap, uint64_t *trace_len) {
+                   uint32_t *trace, uint64_t trace_cap, uint64_t *trace_len, int count_only) {
     if (k < 3 || k > 64) return OR_EINVAL;
     oracle_counters local;
     if (!counters) counters = &local;
@@ -554,7 +566,7 @@ int oracle_sdegree(uint32_t n, const uint64_t *rp, const uint32_t *col, uint32_t
     counters->max_outdeg = dag_max_outdeg(n, &D);
     sink S;
     memset(&S, 0, sizeof(S));
-    S.k = k; S.per_root = per_root;
+    S.k = k; S.per_root = per_root; S.count_only = count_only;
     S.out = out ? out + wpre * k : 0;
     S.cap = out ? cap - wpre : 0;
     sdeg_ctx c;
@@ -695,8 +707,10 @@ static void bitcol_list(bitcol_ctx *c, uint32_t l, uint32_t nR, const uint32_t *
         c->cnt->bitjoin_words += c->nw;
         if (l == 2) {
             c->R[nR] = c->ids[v];
-            for (uint32_t w = 0; w < c->h; w++)
-                if ((Cp[w / c->L] >> (w % c->L)) & 1u) { c->R[nR + 1] = c->ids[w]; sink_emit(c->S, c->R); }
+            if (c->S->count_only) sink_add(c->S, size);
+            else
+                for (uint32_t w = 0; w < c->h; w++)
+                    if ((Cp[w / c->L] >> (w % c->L)) & 1u) { c->R[nR + 1] = c->ids[w]; sink_emit(c->S, c->R); }
         } else if (size >= l - 1) {
             c->R[nR] = c->ids[v];
             bitcol_list(c, l - 1, nR + 1, Cp);
@@ -707,7 +721,8 @@ static void bitcol_list(bitcol_ctx *c, uint32_t l, uint32_t nR, const uint32_t *
 int oracle_bitcol(uint32_t n, const uint64_t *rp, const uint32_t *col, uint32_t k, int preprocess,
                   uint32_t L, const uint32_t *roots, uint32_t nroots,
                   uint64_t *count, uint64_t *checksum, uint64_t *per_root,
-                  oracle_counters *counters, uint32_t *out, uint64_t cap, uint64_t *written) {
+                  oracle_counters *counters, uint32_t *out, uint64_t cap, uint64_t *written,
+                  int count_only) {
     if (k < 3 || k > 64 || L < 1 || L > 32) return OR_EINVAL;
     oracle_counters local;
     if (!counters) counters = &local;
@@ -731,7 +746,7 @@ int oracle_bitcol(uint32_t n, const uint64_t *rp, const uint32_t *col, uint32_t 
     uint32_t nwmax = (hmax + L - 1) / L + 1;
     sink S;
     memset(&S, 0, sizeof(S));
-    S.k = k; S.per_root = per_root;
+    S.k = k; S.per_root = per_root; S.count_only = count_only;
     S.out = out ? out + wpre * k : 0;
     S.cap = out ? cap - wpre : 0;
     bitcol_ctx c;
@@ -742,9 +757,10 @@ int oracle_bitcol(uint32_t n, const uint64_t *rp, const uint32_t *col, uint32_t 
     uint32_t *colour = (uint32_t *)malloc(((size_t)hmax + 1) * sizeof(uint32_t));
     uint32_t *order = (uint32_t *)malloc(((size_t)hmax + 1) * sizeof(uint32_t));
     uint32_t *C0 = (uint32_t *)malloc((size_t)nwmax * sizeof(uint32_t));
+    uint32_t *pos = (uint32_t *)calloc((size_t)n + 1, sizeof(uint32_t));
     c.buf = (uint32_t **)calloc(k + 1, sizeof(uint32_t *));
     for (uint32_t i = 0; c.buf && i <= k; i++) c.buf[i] = (uint32_t *)malloc((size_t)nwmax * sizeof(uint32_t));
-    if (!adj || !B || !colour || !order || !C0 || !c.buf) rc = OR_ENOMEM;
+    if (!adj || !B || !colour || !order || !C0 || !pos || !c.buf) rc = OR_ENOMEM;
     for (uint32_t i = 0; !rc && i <= k; i++) if (!c.buf[i]) rc = OR_ENOMEM;
     uint32_t total_roots = roots ? nroots : n;
     for (uint32_t r = 0; !rc && r < total_roots; r++) {
@@ -754,12 +770,21 @@ int oracle_bitcol(uint32_t n, const uint64_t *rp, const uint32_t *col, uint32_t 
         if (!P.alive[u] || h < k - 1) continue;
         counters->roots++;
         const uint32_t *Nu = D.oadj + D.optr[u];
-        /* G_u: undirected subgraph induced by N+_u (Section VII-B) */
+        /* G_u: undirected subgraph induced by N+_u (Section VII-B).  Every
+         * edge {a, b} of G_u is oriented by the DAG, so it lies in exactly one
+         * of the out-lists N+_a, N+_b: scanning the out-lists of the members
+         * of N+_u (pos marks membership) finds each edge once. */
+        memset(adj, 0, (size_t)h * h);
+        for (uint32_t i = 0; i < h; i++) pos[Nu[i]] = i + 1;
         for (uint32_t i = 0; i < h; i++) {
-            counters->build_reads += rp[Nu[i] + 1] - rp[Nu[i]];
-            for (uint32_t j = 0; j < h; j++)
-                adj[(size_t)i * h + j] = (i != j && is_adjacent(rp, col, Nu[i], Nu[j])) ? 1 : 0;
+            uint32_t a = Nu[i];
+            counters->build_reads += D.optr[a + 1] - D.optr[a];
+            for (uint64_t e = D.optr[a]; e < D.optr[a + 1]; e++) {
+                uint32_t j = pos[D.oadj[e]];
+                if (j) { adj[(size_t)i * h + (j - 1)] = 1; adj[(size_t)(j - 1) * h + i] = 1; }
+            }
         }
+        for (uint32_t i = 0; i < h; i++) pos[Nu[i]] = 0;
         greedy_colouring(h, adj, order, colour);       /* ColorOrdering(G_u) */
         uint32_t nw = (h + L - 1) / L;
         bit_encode(h, adj, colour, L, nw, B);           /* BitEncode */
@@ -770,7 +795,7 @@ int oracle_bitcol(uint32_t n, const uint64_t *rp, const uint32_t *col, uint32_t 
         bitcol_list(&c, k - 1, 1, C0);
     }
     for (uint32_t i = 0; c.buf && i <= k; i++) free(c.buf[i]);
-    free(c.buf); free(adj); free(B); free(colour); free(order); free(C0);
+    free(c.buf); free(adj); free(B); free(colour); free(order); free(C0); free(pos);
     free_dag(&D);
     free(P.alive);
     if (rc) return rc;

@@ -62,7 +62,8 @@ kcl_status dev_alloc(T **p, size_t count) {
 void free_workspace(Workspace &w) {
     void *ptrs[] = {w.alive, w.alive_core, w.cdeg, w.key, w.peel_deg, w.frontier_a, w.frontier_b,
                     w.parent, w.comp_n, w.comp_sdeg, w.comp_flag, w.outdeg, w.optr, w.oadj,
-                    w.roots, w.hist, w.scan_tmp, w.queue, w.members, w.comp_slot, w.arena, w.res};
+                    w.roots, w.hist, w.scan_tmp, w.queue, w.members, w.comp_slot, w.arena, w.res,
+                    w.peel};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (w.h_res) cudaFreeHost(w.h_res);
@@ -96,6 +97,7 @@ kcl_status ensure_workspace(kcl_graph *g) {
     KCL_TRY(dev_alloc(&w.members, n));
     KCL_TRY(dev_alloc(&w.comp_slot, n));
     KCL_TRY(dev_alloc(&w.res, 1));
+    KCL_TRY(dev_alloc(&w.peel, 1));
     if (cudaMallocHost((void **)&w.h_res, sizeof(DevResult)) != cudaSuccess) {
         (void)cudaGetLastError();
         w.h_res = nullptr;
@@ -186,6 +188,25 @@ kcl_status status_from_device(uint32_t st) {
     return KCL_OK;
 }
 
+// Degeneracy peel in one cooperative launch (false: not launchable here, the
+// caller falls back to one launch per round).
+bool run_peel_coop(kcl_graph *g, StageTimer &T) {
+    Workspace &w = g->ws;
+    cudaStream_t s = g->stream;
+    if (cudaMemsetAsync(w.peel, 0, sizeof(PeelCtl), s) != cudaSuccess ||
+        cudaMemsetAsync(&w.peel->minv, 0xFF, sizeof(unsigned), s) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return false;
+    }
+    int l = launch_peel_coop(g, w, w.peel, s);
+    if (l < 0) {
+        (void)cudaGetLastError();
+        return false;
+    }
+    T.add(2, l);
+    return true;
+}
+
 // Stages 0-2.  listing: enumerate Pre-List cliques into the ring.
 kcl_status run_front(kcl_graph *g, uint32_t k, kcl_ordering ord, const kcl_ring *ring, bool listing,
                      StageTimer &T, FrontEnd &fe) {
@@ -224,6 +245,11 @@ kcl_status run_front(kcl_graph *g, uint32_t k, kcl_ordering ord, const kcl_ring 
     T.begin(2);
     if (ord == KCL_ORDER_DEGREE) {
         T.add(2, launch_degree_key(g, w, s));
+    } else if (run_peel_coop(g, T)) {
+        uint32_t err = 0;
+        KCL_CK(cudaMemcpyAsync(&err, &w.peel->error, sizeof(err), cudaMemcpyDeviceToHost, s));
+        KCL_CK(cudaStreamSynchronize(s));
+        if (err) return KCL_ETIMEOUT;
     } else {
         T.add(2, launch_peel_init(g, w, s));
         uint32_t remaining = 0;

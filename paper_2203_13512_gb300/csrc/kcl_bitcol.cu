@@ -1,24 +1,27 @@
-// BitCol on the GPU (Algorithm 6, Section VII): for every root u of the
-// degeneracy DAG with d+_u >= k-1, one warp
+// BitCol on the GPU (Algorithm 6, Section VII).  For every root u of the
+// degeneracy DAG with d+_u >= k-1 a group of threads (one warp for small
+// out-degrees, one CTA for large ones)
 //   1. builds G_u, the undirected subgraph induced by N+_u (Section VII-B), as
-//      bit-rows over the index space of N+_u (ascending id) -- each edge of
-//      G_u lies in exactly one DAG out-list, so the warp scans the out-lists
-//      of N+_u once and binary-searches each entry in N+_u;
+//      bit-rows over the index space of N+_u (ascending id): each edge of G_u
+//      lies in exactly one DAG out-list, so the group streams the out-lists of
+//      N+_u once (flattened, load-balanced over lanes) and probes each entry
+//      in a hash table of N+_u;
 //   2. colours G_u greedily in (degree descending, index ascending) order,
 //      colours from 1 (Section VII-A, Example 6);
 //   3. re-indexes G_u by colour (colour classes become contiguous index
-//      ranges) and encodes the colour-ordered DAG: B'(p) holds the
-//      out-neighbours of p, all of which sit below start[colour(p)]
-//      (BitEncode, Section VII-C);
-//   4. runs BitColList as an explicit-stack DFS: at level l only candidates
-//      with colour >= l are expanded (Lemma 1 pruning, which the re-indexing
-//      turns into a prefix test), C' = B'(v) AND C (BitJoin), recursion when
-//      |C'| >= l-1, and at l = 2 each w in C' closes a clique.
+//      ranges, start[c] = first index of colour c) and encodes the colour-
+//      ordered DAG: B'(p) holds the out-neighbours of p, all below
+//      start[colour(p)] (BitEncode, Section VII-C);
+//   4. runs BitColList as explicit-stack DFS: at level l only candidates of
+//      colour >= l are expanded (Lemma 1 pruning, a prefix test after the
+//      re-indexing), C' = B'(v) AND C (BitJoin), recursion when |C'| >= l-1,
+//      and at l = 2 each w in C' closes a clique.  In the CTA form the
+//      first-level children of the root are shared out to the CTA's warps.
 // Lanes evaluate candidates in parallel (lane b takes bit b of a candidate
-// word) and each lane ANDs + POPCs the words of its candidate's row; rows
-// have an odd word stride so 32 lanes reading 32 different rows hit 32
-// different shared-memory banks.  The word size is 32 (the paper's L = 24 on
-// its CPU); the results do not depend on it.
+// word) and each lane ANDs + POPCs the words of its candidate's row that can
+// be non-zero; rows have an odd word stride so 32 lanes reading 32 rows hit
+// 32 different shared-memory banks.  The word size is 32 bits (the paper
+// uses 24 on its CPU); results do not depend on it.
 #include "kcl_internal.cuh"
 
 namespace kcl {
@@ -27,29 +30,78 @@ namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
 
-// Per-warp scratch layout (32-bit words) for subproblems of at most 32*W
-// vertices, with a DFS stack for k levels.
-struct Lay {
-    uint32_t W, D, WP, NBR, PRE, IDS, U16, ROWS_A, ROWS_B, STACK, total;
+// ------------------------------------------------------------- layouts
+// Subproblem region (words) for at most D = 32 W vertices.  A (undirected
+// rows, old index) and B (colour-DAG rows, new index) may live in a global
+// arena instead (a_global / b_global), in which case they take no room here.
+struct SubLay {
+    uint32_t W, D, WP, NBR, PRE, IDS, HK, HV, U16, META, PEND, A, B, total;
 };
 
-__host__ __device__ inline Lay make_layout(uint32_t W, uint32_t k) {
-    Lay L;
+__host__ __device__ inline SubLay sub_layout(uint32_t W, bool a_global, bool b_global) {
+    SubLay L;
     L.W = W;
     L.D = 32 * W;
     L.WP = (W & 1) ? W : W + 1;
     L.NBR = 0;
-    L.PRE = L.NBR + L.D;
-    L.IDS = L.PRE + L.D + 1;
-    L.U16 = L.IDS + L.D;
-    uint32_t u16_words = (4 * L.D + 2 + 1) / 2;  // colour_old, old2new, colp, start
-    L.ROWS_A = L.U16 + u16_words;
-    L.ROWS_B = L.ROWS_A + L.D * L.WP;
-    L.STACK = L.ROWS_B + L.D * L.WP;
-    L.total = L.STACK + k * (2 * W + 2) + 32;
-    L.total = (L.total + 3) & ~3u;
+    L.PRE = L.NBR + L.D;        // D + 1
+    L.IDS = L.PRE + L.D + 1;    // D
+    L.HK = L.IDS + L.D;         // 2D hash keys
+    L.HV = L.HK + 2 * L.D;      // 2D hash values (u16)
+    L.U16 = L.HV + L.D;         // colour_old, old2new, colp (D each), start (D + 2), u16
+    L.META = L.U16 + (4 * L.D + 2 + 1) / 2;
+    L.PEND = L.META + 8;        // first-level children (u16, D)
+    uint32_t end = L.PEND + (L.D + 1) / 2;
+    L.A = a_global ? 0 : end;
+    if (!a_global) end += L.D * L.WP;
+    L.B = b_global ? 0 : end;
+    if (!b_global) end += L.D * L.WP;
+    L.total = (end + 3) & ~3u;
     return L;
 }
+
+// Per-warp DFS stack: C and pending-children bitmaps per depth, path, cursor.
+__host__ __device__ inline uint32_t dfs_words(uint32_t W, uint32_t k) {
+    return (k * (2 * W + 2) + 32 + 3) & ~3u;
+}
+
+struct Sub {
+    uint32_t *nbr, *pre, *ids, *hk, *meta;
+    uint16_t *hv, *colour_old, *old2new, *colp, *start, *pend;
+    uint32_t *A, *B;
+};
+
+__device__ inline Sub sub_ptrs(uint32_t *S, const SubLay &L, uint32_t *Ag, uint32_t *Bg) {
+    Sub s;
+    s.nbr = S + L.NBR;
+    s.pre = S + L.PRE;
+    s.ids = S + L.IDS;
+    s.hk = S + L.HK;
+    s.hv = reinterpret_cast<uint16_t *>(S + L.HV);
+    s.colour_old = reinterpret_cast<uint16_t *>(S + L.U16);
+    s.old2new = s.colour_old + L.D;
+    s.colp = s.old2new + L.D;
+    s.start = s.colp + L.D;
+    s.meta = S + L.META;
+    s.pend = reinterpret_cast<uint16_t *>(S + L.PEND);
+    s.A = Ag ? Ag : S + L.A;
+    s.B = Bg ? Bg : S + L.B;
+    return s;
+}
+
+// A group working on one subproblem: NW = 1 is a single warp, NW > 1 the
+// whole CTA (blockDim.x threads, at most NW warps).
+template <int NW>
+struct Grp {
+    static __device__ __forceinline__ uint32_t size() { return NW == 1 ? 32u : blockDim.x; }
+    static __device__ __forceinline__ uint32_t nwarps() { return NW == 1 ? 1u : (blockDim.x >> 5); }
+    static __device__ __forceinline__ uint32_t tid() { return NW == 1 ? lane_id() : threadIdx.x; }
+    static __device__ __forceinline__ uint32_t warp() { return NW == 1 ? 0u : (threadIdx.x >> 5); }
+    static __device__ __forceinline__ void sync() {
+        if (NW == 1) __syncwarp();
+        else __syncthreads();
+    }
+};
 
 __device__ __forceinline__ uint32_t warp_incl_scan(uint32_t x) {
     const unsigned lane = lane_id();
@@ -61,334 +113,367 @@ __device__ __forceinline__ uint32_t warp_incl_scan(uint32_t x) {
     return x;
 }
 
-__device__ void warp_bitonic_sort(uint32_t *a, uint32_t n) {
-    const unsigned lane = lane_id();
-    for (uint32_t size = 2; size <= n; size <<= 1)
+// --------------------------------------------------------------- build
+// Steps 1-3 above; leaves B', colp, start, ids and meta[0] = ncol.
+template <int NW, int WT>
+__device__ void build_sub(uint32_t d, uint32_t base, uint32_t Wrt, const uint32_t *__restrict__ optr,
+                          const uint32_t *__restrict__ oadj, const Sub &s) {
+    using G = Grp<NW>;
+    const uint32_t W = WT ? (uint32_t)WT : Wrt;
+    const uint32_t WP = (W & 1) ? W : W + 1;
+    const uint32_t tid = G::tid(), lane = lane_id(), warp = G::warp();
+
+    // out-list lengths of N+_u (scanned below), row starts, zero rows
+    for (uint32_t i = tid; i < d; i += G::size()) {
+        uint32_t v = oadj[base + i];
+        s.nbr[i] = v;
+        uint32_t r0 = optr[v];
+        s.ids[i] = r0;
+        s.pre[i] = optr[v + 1] - r0;
+    }
+    for (uint32_t i = tid; i < d * WP; i += G::size()) {
+        s.A[i] = 0;
+        s.B[i] = 0;
+    }
+    G::sync();
+    if (warp == 0) {
+        uint32_t running = 0;
+        for (uint32_t c0 = 0; c0 < d; c0 += 32) {
+            uint32_t i = c0 + lane;
+            uint32_t x = i < d ? s.pre[i] : 0;
+            uint32_t incl = warp_incl_scan(x);
+            if (i < d) s.pre[i] = running + incl - x;
+            running += __shfl_sync(kFull, incl, 31);
+        }
+        if (lane == 0) s.pre[d] = running;
+    }
+    uint32_t T, hshift;
+    hash_size(d, &T, &hshift);
+    for (uint32_t i = tid; i < T; i += G::size()) s.hk[i] = kHashEmpty;
+    G::sync();
+    for (uint32_t i = tid; i < d; i += G::size()) {
+        uint32_t key = s.nbr[i], h = hash_slot(key, hshift);
+        while (atomicCAS(&s.hk[h], kHashEmpty, key) != kHashEmpty) h = (h + 1) & (T - 1);
+        s.hv[h] = (uint16_t)i;
+    }
+    G::sync();
+
+    // G_u adjacency: stream the out-lists of N+_u as one flattened sequence
+    const uint32_t total = s.pre[d];
+    const uint32_t lo_id = s.nbr[0], hi_id = s.nbr[d - 1];
+    uint32_t a0 = 0;
+    for (uint32_t c = warp * 32; c < total; c += G::size()) {
+        if (NW > 1) {  // row holding element c (largest a with pre[a] <= c)
+            uint32_t lo = a0, hi = d;
+            while (hi - lo > 1) {
+                uint32_t m = (lo + hi) >> 1;
+                if (s.pre[m] <= c) lo = m; else hi = m;
+            }
+            a0 = lo;
+        }
+        const uint32_t e = c + lane;
+        uint32_t a = a0;
+        if (e < total) {
+            while (s.pre[a + 1] <= e) a++;
+            uint32_t w = oadj[s.ids[a] + (e - s.pre[a])];
+            if (w >= lo_id && w <= hi_id) {
+                int x = hash_find(s.hk, s.hv, T, hshift, w);
+                if (x >= 0) {
+                    atomicOr(&s.A[a * WP + ((uint32_t)x >> 5)], 1u << (x & 31));
+                    atomicOr(&s.A[(uint32_t)x * WP + (a >> 5)], 1u << (a & 31));
+                }
+            }
+        }
+        if (NW == 1) a0 = __shfl_sync(kFull, a, 31);
+    }
+    G::sync();
+
+    // colouring order: degree in G_u descending, index ascending (bitonic sort)
+    uint32_t P2 = 1;
+    while (P2 < d) P2 <<= 1;
+    for (uint32_t i = tid; i < P2; i += G::size()) {
+        uint32_t key = 0xFFFFFFFFu;
+        if (i < d) {
+            uint32_t deg = 0;
+            for (uint32_t t = 0; t < W; t++) deg += __popc(s.A[i * WP + t]);
+            key = ((0xFFFFu - deg) << 16) | i;
+        }
+        s.pre[i] = key;
+    }
+    G::sync();
+    for (uint32_t size = 2; size <= P2; size <<= 1)
         for (uint32_t stride = size >> 1; stride > 0; stride >>= 1) {
-            for (uint32_t i = lane; i < n; i += 32) {
+            for (uint32_t i = tid; i < P2; i += G::size()) {
                 uint32_t j = i ^ stride;
                 if (j > i) {
                     bool up = (i & size) == 0;
-                    uint32_t x = a[i], y = a[j];
-                    if ((x > y) == up) { a[i] = y; a[j] = x; }
+                    uint32_t x = s.pre[i], y = s.pre[j];
+                    if ((x > y) == up) { s.pre[i] = y; s.pre[j] = x; }
                 }
+            }
+            G::sync();
+        }
+
+    // greedy colouring (one warp); colour class c is kept as row c-1 of B
+    if (warp == 0) {
+        uint32_t ncol = 0;
+        for (uint32_t t = 0; t < d; t++) {
+            uint32_t v = s.pre[t] & 0xFFFFu;
+            uint32_t chosen = 0;
+            for (uint32_t c0 = 0;; c0 += 32) {
+                uint32_t c = c0 + lane + 1;
+                bool fits = false;
+                if (c <= ncol) {
+                    uint32_t acc = 0;
+                    for (uint32_t w = 0; w < W; w++) acc |= s.A[v * WP + w] & s.B[(c - 1) * WP + w];
+                    fits = acc == 0;
+                } else if (c == ncol + 1) {
+                    fits = true;
+                }
+                unsigned m = __ballot_sync(kFull, fits);
+                if (m) { chosen = c0 + __ffs(m); break; }
+            }
+            if (chosen > ncol) ncol = chosen;
+            if (lane == 0) {
+                s.B[(chosen - 1) * WP + (v >> 5)] |= 1u << (v & 31);
+                s.colour_old[v] = (uint16_t)chosen;
             }
             __syncwarp();
         }
+        // start[c]: first index of colour c in the colour-sorted order
+        uint32_t run = 0;
+        for (uint32_t c0 = 0; c0 < ncol; c0 += 32) {
+            uint32_t c = c0 + lane + 1;
+            uint32_t sz = 0;
+            if (c <= ncol)
+                for (uint32_t w = 0; w < W; w++) sz += __popc(s.B[(c - 1) * WP + w]);
+            uint32_t incl = warp_incl_scan(sz);
+            if (c <= ncol) s.start[c] = (uint16_t)(run + incl - sz);
+            run += __shfl_sync(kFull, incl, 31);
+        }
+        if (lane == 0) {
+            s.start[0] = 0;
+            s.start[ncol + 1] = (uint16_t)d;
+            s.meta[0] = ncol;
+        }
+    }
+    G::sync();
+    for (uint32_t i = tid; i < d; i += G::size()) {
+        uint32_t c = s.colour_old[i];
+        const uint32_t *cls = s.B + (c - 1) * WP;
+        uint32_t r = 0;
+        for (uint32_t w = 0; w < (i >> 5); w++) r += __popc(cls[w]);
+        r += __popc(cls[i >> 5] & ((1u << (i & 31)) - 1u));
+        uint32_t p = s.start[c] + r;
+        s.old2new[i] = (uint16_t)p;
+        s.colp[p] = (uint16_t)c;
+        s.ids[p] = s.nbr[i];
+    }
+    G::sync();
+    for (uint32_t i = tid; i < d * WP; i += G::size()) s.B[i] = 0;
+    G::sync();
+    // B'(p): out-neighbours (lower colour = index below start[colour]); one
+    // thread per row, so no two threads write the same row
+    for (uint32_t i = tid; i < d; i += G::size()) {
+        uint32_t p = s.old2new[i];
+        uint32_t lim = s.start[s.colour_old[i]];
+        uint32_t *row = s.B + p * WP;
+        for (uint32_t w = 0; w < W; w++) {
+            uint32_t m = s.A[i * WP + w];
+            while (m) {
+                uint32_t j = w * 32 + (__ffs(m) - 1);
+                m &= m - 1;
+                uint32_t q = s.old2new[j];
+                if (q < lim) row[q >> 5] |= 1u << (q & 31);
+            }
+        }
+    }
+    G::sync();
 }
 
+// ----------------------------------------------------------------- DFS
 struct Emit {
     uint32_t *ring;
     unsigned long long capacity;
     int wrap;
 };
 
-// One root: build, colour, encode, DFS.  Counts accumulate per lane in
-// `cnt`; in listing mode hashes accumulate in `cks`.
-template <int WT, bool LIST>
-__device__ void bitcol_root(uint32_t u, uint32_t k, uint32_t Wrt, const uint32_t *__restrict__ optr,
-                            const uint32_t *__restrict__ oadj, uint32_t *S, const Emit &em,
-                            DevResult *res, unsigned long long &cnt, unsigned long long &cks) {
-    const uint32_t W = WT ? (uint32_t)WT : Wrt;
-    const Lay L = make_layout(W, k);
-    const uint32_t WP = L.WP;
+struct View {  // read-only view of a built subproblem, per warp
+    const uint32_t *B;
+    const uint16_t *colp, *start;
+    const uint32_t *ids;
+    uint32_t d, W, WP, ncol, u, k;
+};
+
+__device__ __forceinline__ uint32_t start_of(const View &v, uint32_t l) {
+    return l <= v.ncol + 1 ? (uint32_t)v.start[l] : v.d;
+}
+
+// bits of C[j] at index >= s
+__device__ __forceinline__ uint32_t cand_word(const uint32_t *C, uint32_t j, uint32_t s) {
+    uint32_t m = C[j];
+    uint32_t lo = j * 32;
+    if (s >= lo + 32) return 0u;
+    if (s > lo) m &= ~((1u << (s - lo)) - 1u);
+    return m;
+}
+
+__device__ __forceinline__ uint32_t row_words(const View &v, uint32_t p, uint32_t cw) {
+    uint32_t wl = (v.start[v.colp[p]] + 31) >> 5;
+    return wl < cw ? wl : cw;
+}
+
+// Leaf (l = 2) over candidate words j0, j0+js, ... < cw: each candidate p
+// closes |B'(p) & C| cliques.  depth = number of path entries below the root.
+template <bool LIST>
+__device__ void leaf(const View &v, const uint32_t *C, uint32_t cw, uint32_t depth, uint32_t j0,
+                     uint32_t js, const uint32_t *path, uint32_t *sortedR, const Emit &em,
+                     DevResult *res, unsigned long long &cnt, unsigned long long &cks) {
     const unsigned lane = lane_id();
-    const uint32_t base = optr[u];
-    const uint32_t d = optr[u + 1] - base;
-
-    uint32_t *nbr = S + L.NBR;
-    uint32_t *pre = S + L.PRE;
-    uint32_t *ids = S + L.IDS;
-    uint16_t *colour_old = reinterpret_cast<uint16_t *>(S + L.U16);
-    uint16_t *old2new = colour_old + L.D;
-    uint16_t *colp = old2new + L.D;
-    uint16_t *start = colp + L.D;  // D + 2 entries
-    uint32_t *A = S + L.ROWS_A;
-    uint32_t *B = S + L.ROWS_B;
-    uint32_t *Cst = S + L.STACK;
-    uint32_t *Pst = Cst + k * W;
-    uint32_t *path = Pst + k * W;
-    uint32_t *cur = path + k;
-    uint32_t *sortedR = cur + k;
-
-    // ---- 1. N+_u, prefix sums of the neighbours' out-degrees, zero rows
-    uint32_t running = 0;
-    for (uint32_t c0 = 0; c0 < d; c0 += 32) {
-        uint32_t i = c0 + lane;
-        uint32_t x = 0;
-        if (i < d) {
-            uint32_t v = oadj[base + i];
-            nbr[i] = v;
-            uint32_t rs = optr[v];
-            ids[i] = rs;  // row start, reused below
-            x = optr[v + 1] - rs;
-        }
-        uint32_t incl = warp_incl_scan(x);
-        if (i < d) pre[i] = running + incl - x;
-        running += __shfl_sync(kFull, incl, 31);
-    }
-    for (uint32_t i = lane; i < d * WP; i += 32) { A[i] = 0; B[i] = 0; }
-    if (lane == 0) pre[d] = running;
-    __syncwarp();
-    const uint32_t total = running;
-    const uint32_t lo_id = nbr[0], hi_id = nbr[d - 1];
-
-    // ---- 2. adjacency of G_u (both directions of every edge)
-    for (uint32_t e = lane; e < total; e += 32) {
-        uint32_t a = 0, b = d;  // largest a with pre[a] <= e
-        while (b - a > 1) {
-            uint32_t m = (a + b) >> 1;
-            if (pre[m] <= e) a = m; else b = m;
-        }
-        uint32_t w = oadj[ids[a] + (e - pre[a])];
-        if (w < lo_id || w > hi_id) continue;
-        uint32_t x = 0, y = d;
-        while (x < y) {
-            uint32_t m = (x + y) >> 1;
-            if (nbr[m] < w) x = m + 1; else y = m;
-        }
-        if (x < d && nbr[x] == w) {
-            atomicOr(&A[a * WP + (x >> 5)], 1u << (x & 31));
-            atomicOr(&A[x * WP + (a >> 5)], 1u << (a & 31));
-        }
-    }
-    __syncwarp();
-
-    // ---- 3. colouring order: degree in G_u descending, index ascending
-    uint32_t P2 = 1;
-    while (P2 < d) P2 <<= 1;
-    for (uint32_t i = lane; i < P2; i += 32) {
-        uint32_t key = 0xFFFFFFFFu;
-        if (i < d) {
-            uint32_t deg = 0;
-            for (uint32_t t = 0; t < W; t++) deg += __popc(A[i * WP + t]);
-            key = ((0xFFFFu - deg) << 16) | i;
-        }
-        pre[i] = key;
-    }
-    __syncwarp();
-    warp_bitonic_sort(pre, P2);
-
-    // ---- 4. greedy colouring; colour classes as bitmaps (class c in row c-1 of B)
-    uint32_t ncol = 0;
-    for (uint32_t t = 0; t < d; t++) {
-        uint32_t v = pre[t] & 0xFFFFu;
-        uint32_t chosen = 0;
-        for (uint32_t c0 = 0;; c0 += 32) {
-            uint32_t c = c0 + lane + 1;
-            bool fits = false;
-            if (c <= ncol) {
-                uint32_t acc = 0;
-                for (uint32_t w = 0; w < W; w++) acc |= A[v * WP + w] & B[(c - 1) * WP + w];
-                fits = acc == 0;
-            } else if (c == ncol + 1) {
-                fits = true;
-            }
-            unsigned m = __ballot_sync(kFull, fits);
-            if (m) { chosen = c0 + __ffs(m); break; }
-        }
-        if (chosen > ncol) ncol = chosen;
+    const uint32_t s = start_of(v, 2);
+    if (LIST) {
         if (lane == 0) {
-            B[(chosen - 1) * WP + (v >> 5)] |= 1u << (v & 31);
-            colour_old[v] = (uint16_t)chosen;
-        }
-        __syncwarp();
-    }
-
-    // ---- 5. colour-sorted index: start[c] = first index of colour c
-    for (uint32_t c0 = 0, run = 0; c0 < ncol; c0 += 32) {
-        uint32_t c = c0 + lane + 1;
-        uint32_t sz = 0;
-        if (c <= ncol)
-            for (uint32_t w = 0; w < W; w++) sz += __popc(B[(c - 1) * WP + w]);
-        uint32_t incl = warp_incl_scan(sz);
-        if (c <= ncol) start[c] = (uint16_t)(run + incl - sz);
-        run += __shfl_sync(kFull, incl, 31);
-    }
-    if (lane == 0) {
-        start[0] = 0;
-        start[ncol + 1] = (uint16_t)d;
-    }
-    __syncwarp();
-    for (uint32_t i = lane; i < d; i += 32) {
-        uint32_t c = colour_old[i];
-        const uint32_t *cls = B + (c - 1) * WP;
-        uint32_t r = 0;
-        for (uint32_t w = 0; w < (i >> 5); w++) r += __popc(cls[w]);
-        r += __popc(cls[i >> 5] & ((1u << (i & 31)) - 1u));
-        uint32_t p = start[c] + r;
-        old2new[i] = (uint16_t)p;
-        colp[p] = (uint16_t)c;
-        ids[p] = nbr[i];
-    }
-    __syncwarp();
-
-    // ---- 6. oriented rows B'(p): out-neighbours = lower colour = index < start[colour]
-    for (uint32_t i = lane; i < d * WP; i += 32) B[i] = 0;
-    __syncwarp();
-    for (uint32_t i = lane; i < d; i += 32) {
-        uint32_t p = old2new[i];
-        uint32_t lim = start[colour_old[i]];
-        uint32_t *row = B + p * WP;
-        for (uint32_t w = 0; w < W; w++) {
-            uint32_t m = A[i * WP + w];
-            while (m) {
-                uint32_t j = w * 32 + (__ffs(m) - 1);
-                m &= m - 1;
-                uint32_t q = old2new[j];
-                if (q < lim) row[q >> 5] |= 1u << (q & 31);
-            }
-        }
-    }
-    __syncwarp();
-
-    // ---- 7. BitColList as an explicit-stack DFS
-    auto start_of = [&](uint32_t l) -> uint32_t { return l <= ncol + 1 ? (uint32_t)start[l] : d; };
-    // candidate words: bits of C at index >= s
-    auto cand_word = [&](const uint32_t *C, uint32_t j, uint32_t s) -> uint32_t {
-        uint32_t m = C[j];
-        uint32_t lo = j * 32;
-        if (s >= lo + 32) return 0u;
-        if (s > lo) m &= ~((1u << (s - lo)) - 1u);
-        return m;
-    };
-    // leaf (l = 2): every candidate v closes |B'(v) & C| cliques
-    auto leaf = [&](const uint32_t *C, uint32_t cw, uint32_t depth) {
-        const uint32_t s = start_of(2);
-        if (LIST && lane == 0) {
-            // R = {u} + path[1..depth], sorted ascending (original ids)
-            uint32_t nr = depth + 1;
-            sortedR[0] = u;
-            for (uint32_t t = 1; t < nr; t++) {
-                uint32_t x = ids[path[t]], j = t;
+            sortedR[0] = v.u;
+            for (uint32_t t = 1; t <= depth; t++) {
+                uint32_t x = v.ids[path[t]], j = t;
                 while (j > 0 && sortedR[j - 1] > x) { sortedR[j] = sortedR[j - 1]; j--; }
                 sortedR[j] = x;
             }
         }
-        if (LIST) __syncwarp();
-        for (uint32_t j = 0; j < cw; j++) {
-            uint32_t m = cand_word(C, j, s);
-            if (!m) continue;
-            uint32_t p = j * 32 + lane;
-            uint32_t x = 0;
-            bool mine = (m >> lane) & 1u;
-            if (mine) {
-                const uint32_t *row = B + p * WP;
-                uint32_t wl = (start[colp[p]] + 31) >> 5;
-                if (wl > cw) wl = cw;
-                for (uint32_t t = 0; t < wl; t++) x += __popc(row[t] & C[t]);
+        __syncwarp();
+    }
+    for (uint32_t j = j0; j < cw; j += js) {
+        uint32_t m = cand_word(C, j, s);
+        if (!m) continue;
+        const uint32_t p = j * 32 + lane;
+        const bool mine = (m >> lane) & 1u;
+        uint32_t x = 0;
+        if (mine) {
+            const uint32_t *row = v.B + p * v.WP;
+            uint32_t wl = row_words(v, p, cw);
+            for (uint32_t t = 0; t < wl; t++) x += __popc(row[t] & C[t]);
+        }
+        cnt += x;
+        if (LIST) {
+            uint32_t incl = warp_incl_scan(x);
+            uint32_t tot = __shfl_sync(kFull, incl, 31);
+            unsigned long long slot0 = 0;
+            if (tot && em.ring) {
+                if (lane == 0) slot0 = atomicAdd(&res->emitted, (unsigned long long)tot);
+                slot0 = __shfl_sync(kFull, slot0, 0);
             }
-            cnt += x;
-            if (LIST) {
-                uint32_t incl = warp_incl_scan(x);
-                uint32_t tot = __shfl_sync(kFull, incl, 31);
-                unsigned long long slot0 = 0;
-                if (tot) {
-                    if (lane == 0 && em.ring) slot0 = atomicAdd(&res->emitted, (unsigned long long)tot);
-                    slot0 = __shfl_sync(kFull, slot0, 0);
-                }
-                if (mine && x) {
-                    unsigned long long slot = slot0 + (incl - x);
-                    const uint32_t *row = B + p * WP;
-                    uint32_t a = ids[p];
-                    uint32_t wl = (start[colp[p]] + 31) >> 5;
-                    if (wl > cw) wl = cw;
-                    for (uint32_t t = 0; t < wl; t++) {
-                        uint32_t mm = row[t] & C[t];
-                        while (mm) {
-                            uint32_t q = t * 32 + (__ffs(mm) - 1);
-                            mm &= mm - 1;
-                            uint32_t b = ids[q];
-                            uint32_t e0 = a < b ? a : b, e1 = a < b ? b : a;
-                            uint32_t ex[2] = {e0, e1};
-                            uint32_t rec[KCL_MAX_K];
-                            uint32_t nr = k - 2, ri = 0, ei = 0, o = 0;
-                            while (ri < nr || ei < 2) {
-                                uint32_t r = ri < nr ? sortedR[ri] : 0xFFFFFFFFu;
-                                if (ei < 2 && ex[ei] < r) rec[o++] = ex[ei++];
-                                else rec[o++] = sortedR[ri++];
-                            }
-                            uint64_t h = hash_seed(k);
-                            for (uint32_t z = 0; z < k; z++) h = mix64(h ^ (uint64_t)rec[z]);
-                            cks += h;
-                            if (em.ring) {
-                                unsigned long long sl = slot;
-                                bool ok = true;
-                                if (em.wrap) sl %= em.capacity;
-                                else ok = sl < em.capacity;
-                                if (ok)
-                                    for (uint32_t z = 0; z < k; z++) em.ring[sl * k + z] = rec[z];
-                            }
-                            slot++;
+            if (mine && x) {
+                unsigned long long slot = slot0 + (incl - x);
+                const uint32_t *row = v.B + p * v.WP;
+                const uint32_t a = v.ids[p];
+                const uint32_t wl = row_words(v, p, cw);
+                const uint32_t k = v.k;
+                for (uint32_t t = 0; t < wl; t++) {
+                    uint32_t mm = row[t] & C[t];
+                    while (mm) {
+                        uint32_t q = t * 32 + (__ffs(mm) - 1);
+                        mm &= mm - 1;
+                        uint32_t b = v.ids[q];
+                        uint32_t ex[2] = {a < b ? a : b, a < b ? b : a};
+                        uint32_t rec[KCL_MAX_K];
+                        uint32_t nr = k - 2, ri = 0, ei = 0, o = 0;
+                        while (ri < nr || ei < 2) {
+                            uint32_t r = ri < nr ? sortedR[ri] : 0xFFFFFFFFu;
+                            if (ei < 2 && ex[ei] < r) rec[o++] = ex[ei++];
+                            else rec[o++] = sortedR[ri++];
                         }
+                        uint64_t h = hash_seed(k);
+                        for (uint32_t z = 0; z < k; z++) h = mix64(h ^ (uint64_t)rec[z]);
+                        cks += h;
+                        if (em.ring) {
+                            unsigned long long sl = slot;
+                            bool ok = true;
+                            if (em.wrap) sl %= em.capacity;
+                            else ok = sl < em.capacity;
+                            if (ok)
+                                for (uint32_t z = 0; z < k; z++) em.ring[sl * k + z] = rec[z];
+                        }
+                        slot++;
                     }
                 }
             }
         }
-    };
-    // inner node (l >= 3): pending children = candidates v with |B'(v) & C| >= l-1
-    auto expand = [&](const uint32_t *C, uint32_t cw, uint32_t l, uint32_t *P) {
-        const uint32_t s = start_of(l);
-        for (uint32_t j = 0; j < W; j++) {
-            uint32_t m = j < cw ? cand_word(C, j, s) : 0u;
-            bool ok = false;
-            if ((m >> lane) & 1u) {
-                uint32_t p = j * 32 + lane;
-                const uint32_t *row = B + p * WP;
-                uint32_t wl = (start[colp[p]] + 31) >> 5;
-                if (wl > cw) wl = cw;
-                uint32_t x = 0;
-                for (uint32_t t = 0; t < wl; t++) x += __popc(row[t] & C[t]);
-                ok = x + 1 >= l;
-            }
-            unsigned bal = __ballot_sync(kFull, ok);
-            if (lane == 0) P[j] = bal;
-        }
-        __syncwarp();
-    };
+    }
+}
 
-    const uint32_t dw = (d + 31) >> 5;
-    for (uint32_t w = lane; w < W; w += 32) {
-        uint32_t lo = w * 32;
-        Cst[w] = lo + 32 <= d ? kFull : (lo < d ? ((1u << (d - lo)) - 1u) : 0u);
+// Inner node at level l >= 3: pending children = candidates p with
+// |B'(p) & C| >= l-1, as a bitmap P[0..W).
+__device__ void expand(const View &v, const uint32_t *C, uint32_t cw, uint32_t l, uint32_t *P) {
+    const unsigned lane = lane_id();
+    const uint32_t s = start_of(v, l);
+    for (uint32_t j = 0; j < v.W; j++) {
+        uint32_t m = j < cw ? cand_word(C, j, s) : 0u;
+        bool ok = false;
+        if ((m >> lane) & 1u) {
+            uint32_t p = j * 32 + lane;
+            const uint32_t *row = v.B + p * v.WP;
+            uint32_t wl = row_words(v, p, cw);
+            uint32_t x = 0;
+            for (uint32_t t = 0; t < wl; t++) x += __popc(row[t] & C[t]);
+            ok = x + 1 >= l;
+        }
+        unsigned bal = __ballot_sync(kFull, ok);
+        if (lane == 0) P[j] = bal;
     }
     __syncwarp();
-    const uint32_t l0 = k - 1;
-    if (l0 == 2) {
-        leaf(Cst, dw, 0);
+}
+
+// The subtree below first-level child p0 of the root (C1 = B'(p0)), run by
+// one warp with its own stack.
+template <bool LIST>
+__device__ void dfs_child(const View &v, uint32_t p0, uint32_t *stack, const Emit &em,
+                          DevResult *res, unsigned long long &cnt, unsigned long long &cks) {
+    const unsigned lane = lane_id();
+    const uint32_t W = v.W, k = v.k;
+    uint32_t *Cst = stack;             // k * W
+    uint32_t *Pst = Cst + k * W;       // k * W
+    uint32_t *path = Pst + k * W;      // k
+    uint32_t *cur = path + k;          // k
+    uint32_t *sortedR = cur + k;       // 32
+    const uint32_t dw = (v.d + 31) >> 5;
+    // depth 1: C1 = B'(p0) (the root's candidate set is all of N+_u)
+    uint32_t cw1 = row_words(v, p0, dw);
+    for (uint32_t t = lane; t < W; t += 32) Cst[W + t] = t < cw1 ? v.B[p0 * v.WP + t] : 0u;
+    if (lane == 0) path[1] = p0;
+    __syncwarp();
+    uint32_t l = k - 2;
+    if (l == 2) {
+        leaf<LIST>(v, Cst + W, cw1, 1, 0, 1, path, sortedR, em, res, cnt, cks);
+        __syncwarp();
         return;
     }
-    if (start_of(l0) >= d) return;  // fewer than k-1 colours: no (k-1)-clique in G_u
-    expand(Cst, dw, l0, Pst);
-    if (lane == 0) { cur[0] = 0; path[0] = 0; }
-    uint32_t cwst[KCL_MAX_K];  // words in use per depth (uniform)
-    cwst[0] = dw;
+    expand(v, Cst + W, cw1, l, Pst + W);
+    if (lane == 0) cur[1] = 0;
+    uint32_t cwst[KCL_MAX_K];
+    cwst[1] = cw1;
     __syncwarp();
-    int depth = 0;
-    while (depth >= 0) {
+    int depth = 1;
+    while (depth >= 1) {
         uint32_t *P = Pst + depth * W;
         uint32_t j = cur[depth];
         while (j < W && P[j] == 0) j++;
         if (j >= W) { depth--; continue; }
         uint32_t pw = P[j];
-        uint32_t bit = __ffs(pw) - 1;
-        uint32_t p = j * 32 + bit;
+        uint32_t p = j * 32 + (__ffs(pw) - 1);
         __syncwarp();
         if (lane == 0) { P[j] = pw & (pw - 1); cur[depth] = j; }
         const uint32_t *C = Cst + depth * W;
         uint32_t *Cn = Cst + (depth + 1) * W;
-        uint32_t cw = cwst[depth];
-        uint32_t ncw = (start[colp[p]] + 31) >> 5;
-        if (ncw > cw) ncw = cw;
-        for (uint32_t t = lane; t < W; t += 32) Cn[t] = t < ncw ? (B[p * WP + t] & C[t]) : 0u;
+        uint32_t ncw = row_words(v, p, cwst[depth]);
+        for (uint32_t t = lane; t < W; t += 32) Cn[t] = t < ncw ? (v.B[p * v.WP + t] & C[t]) : 0u;
         if (lane == 0) path[depth + 1] = p;
         __syncwarp();
-        uint32_t l = k - 1 - (uint32_t)(depth + 1);
-        if (l == 2) {
-            leaf(Cn, ncw, depth + 1);
+        uint32_t lc = k - 2 - (uint32_t)depth;  // level of the child
+        if (lc == 2) {
+            leaf<LIST>(v, Cn, ncw, depth + 1, 0, 1, path, sortedR, em, res, cnt, cks);
             __syncwarp();
         } else {
-            expand(Cn, ncw, l, Pst + (depth + 1) * W);
+            expand(v, Cn, ncw, lc, Pst + (depth + 1) * W);
             if (lane == 0) cur[depth + 1] = 0;
             cwst[depth + 1] = ncw;
             __syncwarp();
@@ -397,27 +482,75 @@ __device__ void bitcol_root(uint32_t u, uint32_t k, uint32_t Wrt, const uint32_t
     }
 }
 
-template <int WT, bool LIST, bool GLOBAL>
-__global__ void __launch_bounds__(128) k_bitcol(uint32_t k, uint32_t Wrt, const uint32_t *__restrict__ optr,
-                                               const uint32_t *__restrict__ oadj,
-                                               const uint32_t *__restrict__ roots, uint32_t begin,
-                                               uint32_t end, unsigned *queue, uint32_t *arena,
-                                               uint32_t words_per_warp, Emit em,
-                                               unsigned long long *per_root, DevResult *res) {
+// First-level children of the root: p >= start[k-1] with |B'(p)| >= k-2,
+// written to pend in descending index order (heaviest first); returns count.
+template <int NW>
+__device__ uint32_t root_children(const View &v, const Sub &s) {
+    using G = Grp<NW>;
+    const uint32_t l0 = v.k - 1;
+    const uint32_t st = start_of(v, l0);
+    if (G::warp() == 0) {
+        const unsigned lane = lane_id();
+        const uint32_t dw = (v.d + 31) >> 5;
+        uint32_t n = 0;
+        for (uint32_t q = st; q < v.d; q += 32) {
+            bool ok = false;
+            uint32_t p = 0;
+            if (q + lane < v.d) {
+                p = v.d - 1 - (q - st) - lane;  // descending from d-1 down to st
+                const uint32_t *row = v.B + p * v.WP;
+                uint32_t wl = row_words(v, p, dw), x = 0;
+                for (uint32_t t = 0; t < wl; t++) x += __popc(row[t]);
+                ok = x + 2 >= l0;
+            }
+            unsigned m = __ballot_sync(kFull, ok);
+            if (ok) s.pend[n + __popc(m & ((1u << lane) - 1u))] = (uint16_t)p;
+            n += __popc(m);
+        }
+        if (lane == 0) { s.meta[1] = n; s.meta[2] = 0; }
+    }
+    G::sync();
+    return s.meta[1];
+}
+
+// --------------------------------------------------------------- kernels
+// Warp per root: subproblem and stack in this warp's slice of shared memory.
+template <int WT, bool LIST>
+__global__ void __launch_bounds__(128) k_bitcol_warp(uint32_t k, const uint32_t *__restrict__ optr,
+                                                    const uint32_t *__restrict__ oadj,
+                                                    const uint32_t *__restrict__ roots,
+                                                    uint32_t begin, uint32_t end, unsigned *queue,
+                                                    Emit em, unsigned long long *per_root,
+                                                    DevResult *res) {
     extern __shared__ uint32_t smem[];
     const unsigned lane = lane_id();
-    const uint32_t wib = threadIdx.x >> 5;
-    uint32_t *S = GLOBAL ? arena + (size_t)(blockIdx.x * (blockDim.x >> 5) + wib) * words_per_warp
-                         : smem + wib * words_per_warp;
+    const SubLay L = sub_layout(WT, false, false);
+    const uint32_t per_warp = L.total + dfs_words(WT, k);
+    uint32_t *S = smem + (threadIdx.x >> 5) * per_warp;
+    const Sub s = sub_ptrs(S, L, nullptr, nullptr);
+    uint32_t *stack = S + L.total;
     unsigned long long cnt = 0, cks = 0;
     for (;;) {
         uint32_t idx = 0;
         if (lane == 0) idx = atomicAdd(queue, 1u);
         idx = __shfl_sync(kFull, idx, 0);
         if (idx >= end - begin) break;
-        uint32_t u = roots[begin + idx];
-        unsigned long long before = cnt;
-        bitcol_root<WT, LIST>(u, k, Wrt, optr, oadj, S, em, res, cnt, cks);
+        const uint32_t u = roots[begin + idx];
+        const uint32_t base = optr[u], d = optr[u + 1] - base;
+        const unsigned long long before = cnt;
+        build_sub<1, WT>(d, base, WT, optr, oadj, s);
+        View v{s.B, s.colp, s.start, s.ids, d, WT, L.WP, s.meta[0], u, k};
+        if (k == 3) {
+            const uint32_t dw = (d + 31) >> 5;
+            for (uint32_t t = lane; t < WT; t += 32)
+                stack[t] = t < dw ? (t * 32 + 32 <= d ? kFull : (1u << (d - t * 32)) - 1u) : 0u;
+            __syncwarp();
+            uint32_t *path = stack + 2 * k * WT, *sortedR = path + 2 * k;
+            leaf<LIST>(v, stack, dw, 0, 0, 1, path, sortedR, em, res, cnt, cks);
+        } else {
+            const uint32_t nch = root_children<1>(v, s);
+            for (uint32_t i = 0; i < nch; i++) dfs_child<LIST>(v, s.pend[i], stack, em, res, cnt, cks);
+        }
         if (per_root) {
             unsigned long long mine = cnt - before;
             for (int o = 16; o > 0; o >>= 1) mine += __shfl_down_sync(kFull, mine, o);
@@ -435,40 +568,160 @@ __global__ void __launch_bounds__(128) k_bitcol(uint32_t k, uint32_t Wrt, const 
     }
 }
 
-// Root classes by out-degree: d+ <= 32 W for W = 1, 2, 4, 8 in shared memory,
-// then W = 16 .. 128 with the scratch in a global arena (L2-resident).
-constexpr uint32_t kClassW[] = {1, 2, 4, 8, 16, 32, 64, 128};
-constexpr int kNumClasses = 8;
-constexpr int kSmemClasses = 4;
+// CTA per root: the subproblem is built once by the whole CTA (A and/or B in
+// a global arena slice when they do not fit), then the root's first-level
+// children are handed out to the warps, heaviest first.
+template <int NW, bool LIST, bool AG, bool BG>
+__global__ void __launch_bounds__(NW * 32) k_bitcol_cta(uint32_t k, uint32_t W,
+                                                       const uint32_t *__restrict__ optr,
+                                                       const uint32_t *__restrict__ oadj,
+                                                       const uint32_t *__restrict__ roots,
+                                                       uint32_t begin, uint32_t end, unsigned *queue,
+                                                       uint32_t *arena, Emit em,
+                                                       unsigned long long *per_root, DevResult *res) {
+    extern __shared__ uint32_t smem[];
+    __shared__ uint32_t root_idx;
+    const unsigned lane = lane_id();
+    const uint32_t warp = threadIdx.x >> 5;
+    const SubLay L = sub_layout(W, AG, BG);
+    const size_t rows = (size_t)L.D * L.WP;
+    uint32_t *slice = arena + (size_t)blockIdx.x * ((AG ? rows : 0) + (BG ? rows : 0));
+    uint32_t *Ag = AG ? slice : nullptr;
+    uint32_t *Bg = BG ? slice + (AG ? rows : 0) : nullptr;
+    const Sub s = sub_ptrs(smem, L, Ag, Bg);
+    uint32_t *stack = smem + L.total + warp * dfs_words(W, k);
+    unsigned long long cnt = 0, cks = 0;
+    for (;;) {
+        if (threadIdx.x == 0) root_idx = atomicAdd(queue, 1u);
+        __syncthreads();
+        const uint32_t idx = root_idx;
+        __syncthreads();
+        if (idx >= end - begin) break;
+        const uint32_t u = roots[begin + idx];
+        const uint32_t base = optr[u], d = optr[u + 1] - base;
+        const unsigned long long before = cnt;
+        build_sub<NW, 0>(d, base, W, optr, oadj, s);
+        View v{s.B, s.colp, s.start, s.ids, d, W, L.WP, s.meta[0], u, k};
+        if (k == 3) {
+            const uint32_t dw = (d + 31) >> 5;
+            for (uint32_t t = lane; t < W; t += 32)
+                stack[t] = t < dw ? (t * 32 + 32 <= d ? kFull : (1u << (d - t * 32)) - 1u) : 0u;
+            __syncwarp();
+            uint32_t *path = stack + 2 * k * W, *sortedR = path + 2 * k;
+            leaf<LIST>(v, stack, dw, 0, warp, blockDim.x >> 5, path, sortedR, em, res, cnt, cks);
+        } else {
+            const uint32_t nch = root_children<NW>(v, s);
+            for (;;) {
+                uint32_t i = 0;
+                if (lane == 0) i = atomicAdd(&s.meta[2], 1u);
+                i = __shfl_sync(kFull, i, 0);
+                if (i >= nch) break;
+                dfs_child<LIST>(v, s.pend[i], stack, em, res, cnt, cks);
+            }
+        }
+        if (per_root) {
+            unsigned long long mine = cnt - before;
+            for (int o = 16; o > 0; o >>= 1) mine += __shfl_down_sync(kFull, mine, o);
+            if (lane == 0 && mine) atomicAdd(&per_root[u], mine);
+        }
+        __syncthreads();
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        cnt += __shfl_down_sync(kFull, cnt, o);
+        cks += __shfl_down_sync(kFull, cks, o);
+    }
+    if (lane == 0) {
+        add_count(&res->count, &res->count_carry, cnt);
+        if (LIST && cks) atomicAdd(&res->checksum, cks);
+    }
+}
 
-template <int WT, bool LIST, bool GLOBAL>
-void launch_one(uint32_t k, uint32_t W, const kcl_graph *g, Workspace &w, uint32_t begin,
-                uint32_t end, unsigned *queue, const Emit &em, unsigned long long *per_root,
-                int warps_per_block, int blocks, cudaStream_t s) {
-    Lay L = make_layout(W, k);
-    size_t smem = GLOBAL ? 0 : (size_t)warps_per_block * L.total * sizeof(uint32_t);
-    auto kern = k_bitcol<WT, LIST, GLOBAL>;
-    if (!GLOBAL) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    kern<<<blocks, warps_per_block * 32, smem, s>>>(k, W, w.optr, w.oadj, w.roots, begin, end, queue,
-                                                    w.arena, L.total, em, per_root, w.res);
+// --------------------------------------------------------------- classes
+// d+ <= 32 W.  Warp per root for W <= 4, CTA per root above.
+struct ClassCfg {
+    uint32_t W;
+    int nw;      // warps per CTA (CTA form) or warps per block (warp form)
+    bool cta, ag, bg;
+};
+constexpr ClassCfg kClass[] = {
+    {1, 4, false, false, false},  {2, 4, false, false, false},  {4, 4, false, false, false},
+    {8, 8, true, false, false},   {16, 16, true, false, false}, {32, 16, true, true, false},
+    {64, 4, true, true, true},    {128, 2, true, true, true},
+};
+constexpr int kNumClasses = 8;
+
+constexpr size_t kSmemCap = 220 * 1024;
+
+// Warps per CTA for class c at this k: the configured count, reduced until
+// the subproblem plus one DFS stack per warp fits in shared memory.
+int class_warps(int c, uint32_t k) {
+    const ClassCfg &cc = kClass[c];
+    if (!cc.cta) return cc.nw;
+    size_t sub = (size_t)sub_layout(cc.W, cc.ag, cc.bg).total * 4;
+    size_t per = (size_t)dfs_words(cc.W, k) * 4;
+    int nw = cc.nw;
+    while (nw > 1 && sub + nw * per > kSmemCap) nw--;
+    return nw;
+}
+
+size_t class_smem(int c, uint32_t k) {
+    const ClassCfg &cc = kClass[c];
+    if (!cc.cta) return (size_t)cc.nw * (sub_layout(cc.W, false, false).total + dfs_words(cc.W, k)) * 4;
+    return ((size_t)sub_layout(cc.W, cc.ag, cc.bg).total + (size_t)class_warps(c, k) * dfs_words(cc.W, k)) * 4;
+}
+
+size_t class_arena_per_cta(int c) {
+    const ClassCfg &cc = kClass[c];
+    size_t rows = (size_t)32 * cc.W * ((cc.W & 1) ? cc.W : cc.W + 1);
+    return (cc.ag ? rows : 0) + (cc.bg ? rows : 0);
+}
+
+template <int WT, bool LIST>
+void launch_warp(uint32_t k, Workspace &w, uint32_t begin, uint32_t end, unsigned *q, const Emit &em,
+                 unsigned long long *per_root, int wpb, size_t smem, int num_sms, cudaStream_t s) {
+    auto kern = k_bitcol_warp<WT, LIST>;
+    int occ = 0;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, wpb * 32, smem) != cudaSuccess)
+        (void)cudaGetLastError();
+    if (occ < 1) occ = 1;
+    uint32_t blocks = (uint32_t)num_sms * occ;
+    uint32_t need = (end - begin + wpb - 1) / wpb;
+    if (blocks > need) blocks = need;
+    kern<<<blocks, wpb * 32, smem, s>>>(k, w.optr, w.oadj, w.roots, begin, end, q, em, per_root, w.res);
+}
+
+template <int NW, bool LIST, bool AG, bool BG>
+void launch_cta(uint32_t k, uint32_t W, int nw, Workspace &w, uint32_t begin, uint32_t end,
+                unsigned *q, const Emit &em, unsigned long long *per_root, size_t smem,
+                uint32_t blocks, int num_sms, cudaStream_t s) {
+    auto kern = k_bitcol_cta<NW, LIST, AG, BG>;
+    int occ = 0;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, nw * 32, smem) != cudaSuccess)
+        (void)cudaGetLastError();
+    if (occ < 1) occ = 1;
+    uint32_t cap = (uint32_t)num_sms * occ;
+    if (blocks > cap) blocks = cap;
+    kern<<<blocks, nw * 32, smem, s>>>(k, W, w.optr, w.oadj, w.roots, begin, end, q, w.arena, em,
+                                       per_root, w.res);
 }
 
 }  // namespace
 
 int bitcol_classes(uint32_t *limits, int max) {
     int n = kNumClasses < max ? kNumClasses : max;
-    for (int i = 0; i < n; i++) limits[i] = 32 * kClassW[i];
+    for (int i = 0; i < n; i++) limits[i] = 32 * kClass[i].W;
     return n;
 }
 
-// Words of global arena the GLOBAL classes need (for the caller to size it).
+// CTAs that hold an arena slice are capped at one per SM.
 size_t bitcol_arena_words(uint32_t k, int num_sms, uint32_t max_outdeg) {
+    (void)k;
     size_t need = 0;
-    for (int c = kSmemClasses; c < kNumClasses; c++) {
-        if (c > 0 && 32 * kClassW[c - 1] >= max_outdeg) break;
-        Lay L = make_layout(kClassW[c], k);
-        size_t warps = (size_t)num_sms * 4;
-        size_t words = warps * L.total;
+    for (int c = 0; c < kNumClasses; c++) {
+        if (c > 0 && 32 * kClass[c - 1].W >= max_outdeg) break;
+        size_t words = class_arena_per_cta(c) * (size_t)num_sms;
         if (words > need) need = words;
     }
     return need;
@@ -481,33 +734,33 @@ int launch_bitcol(const kcl_graph *g, uint32_t k, Workspace &w, const uint32_t *
     int launches = 0;
     cudaMemsetAsync(w.queue, 0, 64 * sizeof(unsigned), s);
     for (int c = 0; c < n_classes; c++) {
-        uint32_t begin = class_begin[c];
-        uint32_t end = c ? class_begin[c - 1] : class_begin[n_classes];
+        const uint32_t begin = class_begin[c];
+        const uint32_t end = c ? class_begin[c - 1] : class_begin[n_classes];
         if (end <= begin) continue;
-        uint32_t W = kClassW[c];
+        const ClassCfg &cc = kClass[c];
         unsigned *q = w.queue + c;
-        uint32_t nroots = end - begin;
-        if (c < kSmemClasses) {
-            int wpb = W >= 8 ? 2 : 4;
-            int per_sm = W == 1 ? 8 : (W == 2 ? 6 : (W == 4 ? 3 : 3));
-            int blocks = g->num_sms * per_sm;
-            uint32_t need = (nroots + wpb - 1) / wpb;
-            if ((uint32_t)blocks > need) blocks = (int)need;
-#define KCL_BC(WV)                                                                                   \
-    if (la.listing) launch_one<WV, true, false>(k, W, g, w, begin, end, q, em, la.per_root, wpb, blocks, s); \
-    else launch_one<WV, false, false>(k, W, g, w, begin, end, q, em, la.per_root, wpb, blocks, s);
-            if (W == 1) { KCL_BC(1) }
-            else if (W == 2) { KCL_BC(2) }
-            else if (W == 4) { KCL_BC(4) }
-            else { KCL_BC(8) }
-#undef KCL_BC
+        const size_t smem = class_smem(c, k);
+        if (!cc.cta) {
+#define KCL_W(WV)                                                                              \
+    if (la.listing) launch_warp<WV, true>(k, w, begin, end, q, em, la.per_root, cc.nw, smem, g->num_sms, s); \
+    else launch_warp<WV, false>(k, w, begin, end, q, em, la.per_root, cc.nw, smem, g->num_sms, s);
+            if (cc.W == 1) { KCL_W(1) }
+            else if (cc.W == 2) { KCL_W(2) }
+            else { KCL_W(4) }
+#undef KCL_W
         } else {
-            int wpb = 4;
-            int blocks = g->num_sms;
-            uint32_t need = (nroots + wpb - 1) / wpb;
-            if ((uint32_t)blocks > need) blocks = (int)need;
-            if (la.listing) launch_one<0, true, true>(k, W, g, w, begin, end, q, em, la.per_root, wpb, blocks, s);
-            else launch_one<0, false, true>(k, W, g, w, begin, end, q, em, la.per_root, wpb, blocks, s);
+            uint32_t blocks = (cc.ag || cc.bg) ? (uint32_t)g->num_sms : (uint32_t)g->num_sms * 4;
+            if (blocks > end - begin) blocks = end - begin;
+            const int nw = class_warps(c, k);
+#define KCL_C(NWV, AGV, BGV)                                                                          \
+    if (la.listing) launch_cta<NWV, true, AGV, BGV>(k, cc.W, nw, w, begin, end, q, em, la.per_root, smem, blocks, g->num_sms, s); \
+    else launch_cta<NWV, false, AGV, BGV>(k, cc.W, nw, w, begin, end, q, em, la.per_root, smem, blocks, g->num_sms, s);
+            if (cc.nw == 8) { KCL_C(8, false, false) }
+            else if (cc.nw == 16 && !cc.ag) { KCL_C(16, false, false) }
+            else if (cc.nw == 16) { KCL_C(16, true, false) }
+            else if (cc.nw == 4) { KCL_C(4, true, true) }
+            else { KCL_C(2, true, true) }
+#undef KCL_C
         }
         launches++;
     }

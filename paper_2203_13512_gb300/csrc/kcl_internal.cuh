@@ -38,6 +38,14 @@ struct DevResult {
     unsigned int pad;
 };
 
+// Control block of the single-launch degeneracy peel (grid barrier state,
+// round counters, frontier sizes).
+struct PeelCtl {
+    unsigned bar_count, bar_gen, error;
+    unsigned nin, nnext, minv, t, round, remaining, parity;
+    unsigned pad[6];
+};
+
 // Workspace owned by a graph, grown on demand and reused across calls.
 struct Workspace {
     uint8_t *alive = nullptr;        // n
@@ -64,6 +72,7 @@ struct Workspace {
     size_t arena_words = 0;
     DevResult *res = nullptr;
     DevResult *h_res = nullptr;      // pinned host mirror
+    PeelCtl *peel = nullptr;         // single-launch peel control block
     uint32_t n_cap = 0;
     uint64_t nnz_cap = 0;
 };
@@ -114,6 +123,48 @@ __device__ __forceinline__ void add_count(unsigned long long *dst, unsigned long
     if (old + x < old) atomicExch(carry, 1ull);
 }
 
+// Open-addressing hash table (linear probing) of a vertex set held by one
+// warp: ids -> local index.  T is a power of two >= 2 * |set|, so every probe
+// sequence ends at an empty slot.
+constexpr uint32_t kHashEmpty = 0xFFFFFFFFu;
+
+__device__ __forceinline__ uint32_t hash_slot(uint32_t id, uint32_t shift) {
+    return (id * 2654435761u) >> shift;  // Knuth multiplicative hashing
+}
+
+// Build the table for ids[0..d) (distinct) with the whole warp.
+__device__ __forceinline__ void warp_hash_build(const uint32_t *ids, uint32_t d, uint32_t *hk,
+                                                uint16_t *hv, uint32_t T, uint32_t shift) {
+    for (uint32_t i = lane_id(); i < T; i += 32) hk[i] = kHashEmpty;
+    __syncwarp();
+    for (uint32_t i = lane_id(); i < d; i += 32) {
+        uint32_t key = ids[i], h = hash_slot(key, shift);
+        while (atomicCAS(&hk[h], kHashEmpty, key) != kHashEmpty) h = (h + 1) & (T - 1);
+        hv[h] = (uint16_t)i;
+    }
+    __syncwarp();
+}
+
+// Local index of `id`, or -1.
+__device__ __forceinline__ int hash_find(const uint32_t *hk, const uint16_t *hv, uint32_t T,
+                                         uint32_t shift, uint32_t id) {
+    uint32_t h = hash_slot(id, shift);
+    for (;;) {
+        uint32_t k = hk[h];
+        if (k == id) return (int)hv[h];
+        if (k == kHashEmpty) return -1;
+        h = (h + 1) & (T - 1);
+    }
+}
+
+// Smallest power of two >= 2 * d (at least 2) and its hash shift.
+__device__ __forceinline__ void hash_size(uint32_t d, uint32_t *T, uint32_t *shift) {
+    uint32_t t = 2, lg = 1;
+    while (t < 2 * d) { t <<= 1; lg++; }
+    *T = t;
+    *shift = 32 - lg;
+}
+
 // ------------------------------------------------------ host-side launchers
 // Every launcher enqueues on `s` and returns the number of kernel launches.
 
@@ -133,6 +184,8 @@ int launch_peel_select_all(const kcl_graph *g, Workspace &w, uint32_t t, uint32_
 int launch_peel_update(const kcl_graph *g, Workspace &w, const uint32_t *fin, uint32_t nin,
                        uint32_t t, uint32_t round, uint32_t *fout, cudaStream_t s);
 int launch_peel_min(const kcl_graph *g, Workspace &w, cudaStream_t s);
+// Whole degeneracy peel in one cooperative launch; -1 if it cannot launch.
+int launch_peel_coop(const kcl_graph *g, Workspace &w, PeelCtl *ctl, cudaStream_t s);
 int launch_orient(const kcl_graph *g, uint32_t k, Workspace &w, cudaStream_t s);
 int launch_roots(const kcl_graph *g, uint32_t k, Workspace &w, uint32_t max_outdeg,
                  uint32_t *class_begin, const uint32_t *class_limits, int n_classes,

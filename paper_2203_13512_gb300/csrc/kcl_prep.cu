@@ -353,6 +353,126 @@ __global__ void k_peel_update(const uint64_t *__restrict__ rp, const uint32_t *_
     }
 }
 
+// The same peel in one cooperative launch (every block resident): rounds are
+// separated by a grid barrier instead of a kernel boundary and a host round
+// trip.  Control words live in PeelCtl; arrays written during the launch are
+// read with ld.global.cg (L2) so no stale L1 line is used.  Every barrier
+// wait is bounded: past kSpinLimit polls the block records an error, all
+// blocks leave, and the host reports KCL_ETIMEOUT.
+constexpr unsigned long long kSpinLimit = 1ull << 25;
+
+__device__ bool grid_barrier(PeelCtl *c, unsigned nblocks) {
+    __shared__ int ok_s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned *gen = &c->bar_gen;
+        volatile unsigned *err = &c->error;
+        unsigned g = *gen;
+        __threadfence();
+        unsigned arrived = atomicAdd(&c->bar_count, 1u);
+        int ok = 1;
+        if (arrived == nblocks - 1) {
+            atomicExch(&c->bar_count, 0u);
+            __threadfence();
+            atomicAdd(&c->bar_gen, 1u);
+        } else {
+            unsigned long long spins = 0;
+            while (*gen == g) {
+                if (*err) { ok = 0; break; }
+                if (++spins > kSpinLimit) { atomicExch(&c->error, 1u); ok = 0; break; }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+        ok_s = ok && *err == 0;
+    }
+    __syncthreads();
+    return ok_s != 0;
+}
+
+__global__ void __launch_bounds__(512) k_peel_coop(uint32_t n, const uint64_t *__restrict__ rp,
+                                                   const uint32_t *__restrict__ col,
+                                                   const uint8_t *__restrict__ alive,
+                                                   const uint32_t *__restrict__ cdeg, uint32_t *pdeg,
+                                                   uint32_t *key, uint32_t *fa, uint32_t *fb,
+                                                   PeelCtl *c) {
+    const unsigned nblocks = gridDim.x;
+    const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
+    const uint32_t nth = gridDim.x * blockDim.x;
+    const unsigned lane = lane_id();
+    volatile PeelCtl *vc = c;
+    {
+        uint32_t cnt = 0;
+        for (uint32_t v = tid; v < n; v += nth) {
+            pdeg[v] = cdeg[v];
+            key[v] = 0xFFFFFFFFu;
+            cnt += alive[v] ? 1 : 0;
+        }
+        cnt = __reduce_add_sync(0xffffffffu, cnt);
+        if (lane == 0 && cnt) atomicAdd(&c->remaining, cnt);
+    }
+    if (!grid_barrier(c, nblocks)) return;
+    for (;;) {
+        const uint32_t remaining = vc->remaining;
+        if (remaining == 0) break;
+        uint32_t nin = vc->nin;
+        const uint32_t parity = vc->parity;
+        const uint32_t round = vc->round;
+        uint32_t t = vc->t;
+        uint32_t *fin = parity ? fb : fa;
+        uint32_t *fout = parity ? fa : fb;
+        if (nin == 0) {
+            // t rises to the minimum remaining degree; select every vertex at or below it
+            uint32_t mn = 0xFFFFFFFFu;
+            for (uint32_t v = tid; v < n; v += nth)
+                if (alive[v] && __ldcg(&key[v]) == 0xFFFFFFFFu) {
+                    uint32_t d = __ldcg(&pdeg[v]);
+                    mn = d < mn ? d : mn;
+                }
+            mn = __reduce_min_sync(0xffffffffu, mn);
+            if (lane == 0 && mn != 0xFFFFFFFFu) atomicMin(&c->minv, mn);
+            if (!grid_barrier(c, nblocks)) return;
+            const uint32_t mv = vc->minv;
+            if (mv > t) t = mv;
+            for (uint32_t v = tid; v < n; v += nth)
+                if (alive[v] && __ldcg(&key[v]) == 0xFFFFFFFFu && __ldcg(&pdeg[v]) <= t) {
+                    key[v] = round;
+                    fin[atomicAdd(&c->nin, 1u)] = v;
+                }
+            if (!grid_barrier(c, nblocks)) return;
+            nin = vc->nin;
+            if (nin == 0) {  // cannot happen while vertices remain
+                if (tid == 0) atomicExch(&c->error, 2u);
+                return;
+            }
+        }
+        // remove this round's vertices: lower the degrees of their remaining
+        // neighbours; a neighbour reaching <= t joins the next round
+        for (uint32_t i = tid >> 5; i < nin; i += nth >> 5) {
+            uint32_t v = __ldcg(&fin[i]);
+            for (uint64_t e = rp[v] + lane; e < rp[v + 1]; e += 32) {
+                uint32_t w = col[e];
+                if (!alive[w] || __ldcg(&key[w]) != 0xFFFFFFFFu) continue;
+                uint32_t nd = atomicSub(&pdeg[w], 1u) - 1u;
+                if (nd <= t && atomicCAS(&key[w], 0xFFFFFFFFu, round + 1) == 0xFFFFFFFFu)
+                    fout[atomicAdd(&c->nnext, 1u)] = w;
+            }
+        }
+        if (!grid_barrier(c, nblocks)) return;
+        if (tid == 0) {
+            c->remaining = remaining - (nin < remaining ? nin : remaining);
+            c->nin = c->nnext;
+            c->nnext = 0;
+            c->round = round + 1;
+            c->parity = parity ^ 1u;
+            c->t = t;
+            c->minv = 0xFFFFFFFFu;
+            __threadfence();
+        }
+        if (!grid_barrier(c, nblocks)) return;
+    }
+}
+
 // Out-degree in the DAG u -> w iff (key[u], u) < (key[w], w), both alive.
 __device__ __forceinline__ bool eta_less(uint32_t ku, uint32_t u, uint32_t kw, uint32_t w) {
     return ku < kw || (ku == kw && u < w);
@@ -607,6 +727,30 @@ int launch_peel_update(const kcl_graph *g, Workspace &w, const uint32_t *fin, ui
     int grid = grid_for((uint64_t)nin * 32, kBlock, g->num_sms, 32);
     k_peel_update<<<grid, kBlock, 0, s>>>(g->rp, g->col, w.alive, w.peel_deg, w.key, fin, nin, t,
                                           round + 1, fout, &w.res->frontier);
+    return 1;
+}
+
+int launch_peel_coop(const kcl_graph *g, Workspace &w, PeelCtl *ctl, cudaStream_t s) {
+    static int blocks_per_sm = -1;
+    if (blocks_per_sm < 0) {
+        int b = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_peel_coop, 512, 0) != cudaSuccess) b = 0;
+        blocks_per_sm = b > 2 ? 2 : b;
+    }
+    if (blocks_per_sm <= 0) return -1;
+    int blocks = g->num_sms * blocks_per_sm;
+    uint64_t need = ((uint64_t)g->n + 511) / 512;
+    if (need < (uint64_t)blocks) blocks = need ? (int)need : 1;
+    uint32_t n = g->n;
+    const uint64_t *rp = g->rp;
+    const uint32_t *col = g->col;
+    const uint8_t *alive = w.alive;
+    const uint32_t *cdeg = w.cdeg;
+    uint32_t *pdeg = w.peel_deg, *key = w.key, *fa = w.frontier_a, *fb = w.frontier_b;
+    void *args[] = {&n, (void *)&rp, (void *)&col, (void *)&alive, (void *)&cdeg, &pdeg, &key, &fa,
+                    &fb, &ctl};
+    if (cudaLaunchCooperativeKernel((const void *)k_peel_coop, blocks, 512, args, 0, s) != cudaSuccess)
+        return -1;
     return 1;
 }
 

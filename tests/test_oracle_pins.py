@@ -256,3 +256,16 @@ def test_small_workload_all_modes_agree():
     assert (oracle.sdegree(rp, col, 5)["count"], oracle.sdegree(rp, col, 5)["checksum"]) == want
     r = oracle.bitcol(rp, col, 5)
     assert (r["count"], r["checksum"]) == want
+
+
+@pytest.mark.parametrize("k", [3, 4, 6])
+def test_count_only_mode_matches_enumeration(k):
+    # the count-only mode (used to count algorithmic work on large inputs)
+    # must walk the same recursion: same count, counters and per-root values
+    rp, col = kclgen.chung_lu(700, 5000, 2.3, groups=3, group_size=(10, 16), seed=30 + k)
+    for fn, kw in ((oracle.sdegree, {}), (oracle.bitcol, {"L": 32}), (oracle.bitcol, {"L": 24})):
+        full = fn(rp, col, k, per_root=True, **kw)
+        fast = fn(rp, col, k, per_root=True, count_only=True, **kw)
+        assert fast["count"] == full["count"] == oracle.plain(rp, col, k)[0]
+        assert fast["counters"] == full["counters"]
+        assert np.array_equal(fast["per_root"], full["per_root"])
