@@ -50,7 +50,8 @@ typedef enum {
     KCL_ETIMEOUT = 5,   /* a bounded device-side wait gave up */
     KCL_ECUDA = 6,      /* a CUDA runtime call failed */
     KCL_EABORT = 7,     /* aborted by the caller */
-    KCL_ELIMIT = 8      /* a built-in size limit was exceeded (see kcl_strerror) */
+    KCL_ELIMIT = 8,     /* a built-in size limit was exceeded (see kcl_strerror) */
+    KCL_ESIZE = 9       /* input larger than the fixed scratch of an allocation-free call */
 } kcl_status;
 
 /* Vertex orderings of the two algorithms.
@@ -145,6 +146,35 @@ typedef struct {
 } kcl_timing;
 kcl_status kcl_enable_timing(kcl_graph *g, int enable);
 kcl_status kcl_last_timing(const kcl_graph *g, kcl_timing *t);
+
+/* Allocation-free degeneracy ordering (the paper has no counterpart; this is
+ * a library facility).  Some callers must not allocate device memory from
+ * inside their own loops: a serving loop whose latency budget cannot absorb
+ * the device-wide synchronisation that cudaMalloc/cudaFree can cause, or a
+ * host program whose device memory is owned by another allocator under a
+ * fixed budget.  This call computes the same bulk-peel rounds as the
+ * KCL_ORDER_COLOR front end (eta = (round, id); see kcl_stage_info's `key`)
+ * without allocating anything: its scratch (peel degrees, two frontiers and a
+ * control block, about 12 MiB) is a fixed array that every GPU loading the
+ * library holds until the process exits.
+ * n: vertices, at most KCL_NOALLOC_MAX_VERTICES (else KCL_ESIZE, nothing run).
+ * row_ptr, col: the symmetric CSR graph in device memory (as for
+ *   kcl_load_csr; not validated here).
+ * alive: device uint8[n], 1 for the vertices to order.
+ * degree: device uint32[n], each alive vertex's number of alive neighbours.
+ * round_out: device uint32[n] (caller-owned), receives the peel round of each
+ *   alive vertex and 0xFFFFFFFF for the others.
+ * stream: cudaStream_t as void*; the call returns when round_out is ready.
+ * The first call on a device looks up the scratch array's device address
+ * (once per device, with that device current); make that first call before
+ * any stream capture.  Every call on a device reuses the same array (the
+ * control block is cleared at the start of each call), so calls that overlap
+ * on the GPU race and must not be issued concurrently.
+ * Errors: KCL_EINVAL (null pointer), KCL_ESIZE, KCL_ECUDA, KCL_ETIMEOUT. */
+#define KCL_NOALLOC_MAX_VERTICES (1u << 20)
+kcl_status kcl_degeneracy_order_noalloc(uint32_t n, const uint64_t *row_ptr, const uint32_t *col,
+                                        const uint8_t *alive, const uint32_t *degree,
+                                        uint32_t *round_out, void *stream);
 
 /* Human-readable text for a status. */
 const char *kcl_strerror(kcl_status s);

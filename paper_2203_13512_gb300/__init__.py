@@ -249,3 +249,29 @@ def kcl_num_vertices(g):
 
 def kcl_num_edges(g):
     return int(_lib.kcl_num_edges(g.handle))
+
+
+KCL_ESIZE = 9
+KCL_NOALLOC_MAX_VERTICES = 1 << 20
+_lib.kcl_degeneracy_order_noalloc.argtypes = [_U32, _P, _P, _P, _P, _P, _P]
+_lib.kcl_degeneracy_order_noalloc.restype = _I
+
+
+def kcl_degeneracy_order_noalloc(row_ptr, col, alive, degree, round_out, stream=None):
+    """Degeneracy peel rounds without any device allocation.
+
+    For callers that must not allocate device memory from inside their own
+    loops (a serving loop that cannot absorb the synchronisation an
+    allocation may cause, or a program whose device memory belongs to
+    another allocator): all scratch lives in a fixed array inside the
+    library, sized for at most KCL_NOALLOC_MAX_VERTICES vertices.  Every
+    argument is a CUDA tensor: row_ptr int64[n+1], col int32[nnz], alive
+    uint8[n], degree int32[n] (alive-neighbour counts), round_out int32[n]
+    (written).  Calls on one device share the scratch, so they must not
+    overlap on the GPU."""
+    n = row_ptr.numel() - 1
+    st = _lib.kcl_degeneracy_order_noalloc(
+        n, _dev_ptr(row_ptr, "int64"), _dev_ptr(col, "int32"), _dev_ptr(alive, "uint8", n),
+        _dev_ptr(degree, "int32", n), _dev_ptr(round_out, "int32", n),
+        stream if stream is not None else _current_stream())
+    _check(st, "kcl_degeneracy_order_noalloc")

@@ -364,6 +364,7 @@ const char *kcl_strerror(kcl_status s) {
         case KCL_ECUDA: return "CUDA runtime error";
         case KCL_EABORT: return "aborted";
         case KCL_ELIMIT: return "root out-degree above the supported limit";
+        case KCL_ESIZE: return "input larger than the fixed scratch of an allocation-free call";
     }
     return "unknown status";
 }

@@ -4,6 +4,8 @@
 // the out-neighbour CSR of the DAG, plus the root list the listing kernels
 // consume.  Every pass here streams the CSR once: these kernels are bound by
 // HBM bandwidth, so they use warp-per-vertex row scans with coalesced loads.
+#include <mutex>
+
 #include "kcl_internal.cuh"
 
 namespace kcl {
@@ -786,3 +788,97 @@ int launch_roots(const kcl_graph *g, uint32_t k, Workspace &w, uint32_t max_outd
 }
 
 }  // namespace kcl
+
+// ======================================= allocation-free degeneracy ordering
+// Scratch of kcl_degeneracy_order_noalloc: peel degrees, two frontiers and the
+// control block of k_peel_coop for up to KCL_NOALLOC_MAX_VERTICES vertices.
+// It is a fixed device array, so the call never allocates; in host code the
+// array's name is only a stand-in, and its device address is looked up with
+// cudaGetSymbolAddress once per device.
+static constexpr size_t kNoAllocWords =
+    3 * (size_t)KCL_NOALLOC_MAX_VERTICES + sizeof(kcl::PeelCtl) / sizeof(uint32_t);
+static __device__ __align__(256) uint32_t kcl_noalloc_scratch[kNoAllocWords];
+
+namespace {
+constexpr int kNoAllocMaxDevices = 64;
+std::mutex noalloc_mu;
+uint32_t *noalloc_ptr[kNoAllocMaxDevices];
+int noalloc_blocks[kNoAllocMaxDevices];
+
+// Device address of the scratch array and the cooperative grid size for the
+// current device, set up on the first call on that device.
+kcl_status noalloc_setup(uint32_t **ptr, int *blocks) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoAllocMaxDevices) {
+        (void)cudaGetLastError();
+        return KCL_ECUDA;
+    }
+    std::lock_guard<std::mutex> lock(noalloc_mu);
+    if (!noalloc_ptr[dev]) {
+        uint32_t *p = nullptr;
+        if (cudaGetSymbolAddress((void **)&p, kcl_noalloc_scratch) != cudaSuccess || !p) {
+            (void)cudaGetLastError();
+            return KCL_ECUDA;
+        }
+        int sms = 0, per_sm = 0;
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kcl::k_peel_coop, 512, 0) !=
+                cudaSuccess ||
+            sms <= 0 || per_sm <= 0) {
+            (void)cudaGetLastError();
+            return KCL_ECUDA;
+        }
+        noalloc_blocks[dev] = sms * (per_sm > 2 ? 2 : per_sm);
+        noalloc_ptr[dev] = p;
+    }
+    *ptr = noalloc_ptr[dev];
+    *blocks = noalloc_blocks[dev];
+    return KCL_OK;
+}
+}  // namespace
+
+extern "C" kcl_status kcl_degeneracy_order_noalloc(uint32_t n, const uint64_t *row_ptr,
+                                                   const uint32_t *col, const uint8_t *alive,
+                                                   const uint32_t *degree, uint32_t *round_out,
+                                                   void *stream) {
+    if (n > KCL_NOALLOC_MAX_VERTICES) return KCL_ESIZE;
+    if (n == 0) return KCL_OK;
+    if (!row_ptr || !col || !alive || !degree || !round_out) return KCL_EINVAL;
+    uint32_t *S = nullptr;
+    int blocks = 0;
+    kcl_status st = noalloc_setup(&S, &blocks);
+    if (st != KCL_OK) return st;
+    uint64_t need = ((uint64_t)n + 511) / 512;
+    if (need < (uint64_t)blocks) blocks = (int)need;
+    cudaStream_t s = (cudaStream_t)stream;
+    uint32_t *pdeg = S;
+    uint32_t *fa = S + KCL_NOALLOC_MAX_VERTICES;
+    uint32_t *fb = S + 2 * (size_t)KCL_NOALLOC_MAX_VERTICES;
+    kcl::PeelCtl *ctl = reinterpret_cast<kcl::PeelCtl *>(S + 3 * (size_t)KCL_NOALLOC_MAX_VERTICES);
+    // the control block keeps the previous call's contents: clear it (minv
+    // starts at all ones, everything else at zero)
+    if (cudaMemsetAsync(ctl, 0, sizeof(kcl::PeelCtl), s) != cudaSuccess ||
+        cudaMemsetAsync(&ctl->minv, 0xFF, sizeof(unsigned), s) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return KCL_ECUDA;
+    }
+    uint32_t nn = n;
+    const uint64_t *rp = row_ptr;
+    const uint32_t *c = col;
+    const uint8_t *al = alive;
+    const uint32_t *deg = degree;
+    uint32_t *key = round_out;
+    void *args[] = {&nn, (void *)&rp, (void *)&c, (void *)&al, (void *)&deg, &pdeg, &key, &fa, &fb, &ctl};
+    if (cudaLaunchCooperativeKernel((const void *)kcl::k_peel_coop, blocks, 512, args, 0, s) !=
+        cudaSuccess) {
+        (void)cudaGetLastError();
+        return KCL_ECUDA;
+    }
+    unsigned err = 0;
+    if (cudaMemcpyAsync(&err, &ctl->error, sizeof(err), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return KCL_ECUDA;
+    }
+    return err ? KCL_ETIMEOUT : KCL_OK;
+}
