@@ -195,7 +195,7 @@ __device__ void sdegree_root(uint32_t u, uint32_t k, uint32_t D, const uint32_t 
 // Section VII-B, which the paper motivates by the comparisons SDegree wastes
 // on vertices outside N+_u).  Vertices of N+_u get local indices in
 // ascending id order; L(i) = N+_{v_i} intersect N+_u as a sorted list of local
-// indices.  The DFS then intersects short sorted lists in shared memory:
+// indices.  The DFS then intersects short sorted lists:
 //   - lanes evaluate the candidates of a node in parallel, each merging its
 //     L(w) with C (two-pointer merge join, stopping early once the size
 //     bound is met);
@@ -204,9 +204,21 @@ __device__ void sdegree_root(uint32_t u, uint32_t k, uint32_t D, const uint32_t 
 //     ballot-compact the matches in order).
 // The degree prune uses |L(v)| (the out-degree inside G_u), which is at most
 // the global d+_v, so it prunes at least as much and never drops a clique.
+// Roots with d+ <= 128 run one warp each with everything in shared memory;
+// larger ones one CTA each: the CTA builds the lists once and deals the
+// root's first-level children to its warps.
+
+// Warp-per-root layout (words): build scratch, lists, one DFS stack with
+// list capacity D.
 struct LLay {
-    uint32_t D, NBR, LOFS, PRE, RS, HK, HV, LADJ, CL, PD, META, SORTED, total;
+    uint32_t D, NBR, LOFS, PRE, RS, HK, HV, LADJ, STACK, total;
 };
+
+__host__ __device__ inline uint32_t stack_words(uint32_t cap, uint32_t k) {
+    // clist and pend: (k-2) lists of `cap` u16 each; csize, npend, ppos,
+    // path: k words each; sortedR: 32 words
+    return (2 * (((k - 2) * cap + 1) / 2) + 4 * k + 32 + 3) & ~3u;
+}
 
 __host__ __device__ inline LLay make_llayout(uint32_t D, uint32_t k) {
     LLay L;
@@ -219,11 +231,8 @@ __host__ __device__ inline LLay make_llayout(uint32_t D, uint32_t k) {
     L.HK = L.RS + D;          // hash keys (2D)
     L.HV = L.HK + 2 * D;      // hash values, u16 (2D)
     L.LADJ = L.HV + D;
-    L.CL = L.LADJ + (uint32_t)((emax + 1) / 2);
-    L.PD = L.CL + ((k - 1) * D + 1) / 2;
-    L.META = L.PD + ((k - 1) * D + 1) / 2;
-    L.SORTED = L.META + 4 * k;
-    L.total = (L.SORTED + 32 + 3) & ~3u;
+    L.STACK = L.LADJ + (uint32_t)((emax + 1) / 2);
+    L.total = (L.STACK + stack_words(D, k) + 3) & ~3u;
     return L;
 }
 
@@ -275,6 +284,180 @@ __device__ uint32_t warp_intersect16(const uint16_t *a, uint32_t na, const uint1
     return nout;
 }
 
+// A built reduced subproblem and one warp's DFS stack.
+struct LView {
+    const uint32_t *nbr;   // local index -> original id
+    const uint32_t *lofs;  // d + 1 offsets into ladj
+    const uint16_t *ladj;  // reduced out-lists, ascending local indices
+    uint32_t d, u, k;
+    __device__ __forceinline__ uint32_t deg(uint32_t i) const { return lofs[i + 1] - lofs[i]; }
+    __device__ __forceinline__ const uint16_t *list(uint32_t i) const { return ladj + lofs[i]; }
+};
+
+struct LStack {
+    uint16_t *clist, *pend;  // (k-2) lists of cap entries each
+    uint32_t *csize, *npend, *ppos, *path, *sortedR;
+    uint32_t cap;
+};
+
+__device__ inline LStack stack_ptrs(uint32_t *S, uint32_t cap, uint32_t k) {
+    LStack st;
+    st.cap = cap;
+    uint32_t lw = ((k - 2) * cap + 1) / 2;
+    st.clist = reinterpret_cast<uint16_t *>(S);
+    st.pend = reinterpret_cast<uint16_t *>(S + lw);
+    st.csize = S + 2 * lw;
+    st.npend = st.csize + k;
+    st.ppos = st.npend + k;
+    st.path = st.ppos + k;
+    st.sortedR = st.path + k;
+    return st;
+}
+
+// Leaf (l = 2): every candidate w = C[i], i in [b0, b1), closes
+// |L(w) intersect C| cliques.  depth = number of path entries below the root.
+template <bool LIST>
+__device__ void lleaf(const LView &v, const uint16_t *C, uint32_t nC, uint32_t b0, uint32_t b1,
+                      uint32_t depth, const LStack &st, const Emit &em, DevResult *res,
+                      unsigned long long &cnt, unsigned long long &cks) {
+    const unsigned lane = lane_id();
+    if (LIST) {
+        if (lane == 0) {
+            st.sortedR[0] = v.u;
+            for (uint32_t t = 1; t <= depth; t++) {
+                uint32_t x = v.nbr[st.path[t]], j = t;
+                while (j > 0 && st.sortedR[j - 1] > x) { st.sortedR[j] = st.sortedR[j - 1]; j--; }
+                st.sortedR[j] = x;
+            }
+        }
+        __syncwarp();
+    }
+    for (uint32_t s = b0; s < b1; s += 32) {
+        uint32_t i = s + lane;
+        uint32_t x = 0, w = 0;
+        if (i < b1) {
+            w = C[i];
+            uint32_t dw = v.deg(w);
+            if (dw) x = merge_count(v.list(w), dw, C, nC, 0xFFFFFFFFu);
+        }
+        cnt += x;
+        if (LIST) {
+            uint32_t incl = x;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                uint32_t y = __shfl_up_sync(kFull, incl, o);
+                if (lane >= (unsigned)o) incl += y;
+            }
+            uint32_t tot = __shfl_sync(kFull, incl, 31);
+            unsigned long long slot0 = 0;
+            if (tot && em.ring) {
+                if (lane == 0) slot0 = atomicAdd(&res->emitted, (unsigned long long)tot);
+                slot0 = __shfl_sync(kFull, slot0, 0);
+            }
+            if (x) {
+                unsigned long long slot = slot0 + (incl - x);
+                const uint16_t *a = v.list(w);
+                uint32_t na = v.deg(w), ia = 0, ib = 0;
+                uint32_t vid = v.nbr[w];
+                const uint32_t k = v.k;
+                while (ia < na && ib < nC) {
+                    uint32_t p = a[ia], q = C[ib];
+                    if (p == q) {
+                        uint32_t b2 = v.nbr[p];
+                        uint32_t ex[2] = {vid < b2 ? vid : b2, vid < b2 ? b2 : vid};
+                        uint32_t rec[KCL_MAX_K];
+                        uint32_t nr = k - 2, ri = 0, ei = 0, o = 0;
+                        while (ri < nr || ei < 2) {
+                            uint32_t r = ri < nr ? st.sortedR[ri] : 0xFFFFFFFFu;
+                            if (ei < 2 && ex[ei] < r) rec[o++] = ex[ei++];
+                            else rec[o++] = st.sortedR[ri++];
+                        }
+                        uint64_t h = hash_seed(k);
+                        for (uint32_t z = 0; z < k; z++) h = mix64(h ^ (uint64_t)rec[z]);
+                        cks += h;
+                        if (em.ring) {
+                            unsigned long long sl = slot;
+                            bool ok = true;
+                            if (em.wrap) sl %= em.capacity;
+                            else ok = sl < em.capacity;
+                            if (ok)
+                                for (uint32_t z = 0; z < k; z++) em.ring[sl * k + z] = rec[z];
+                        }
+                        slot++;
+                    }
+                    ia += p <= q;
+                    ib += q <= p;
+                }
+            }
+        }
+    }
+}
+
+// Inner node at level l: pending children w in C with |L(w) intersect C| >= l-1.
+__device__ uint32_t lexpand(const LView &v, const uint16_t *C, uint32_t nC, uint32_t l, uint16_t *P) {
+    const unsigned lane = lane_id();
+    uint32_t np = 0;
+    for (uint32_t s = 0; s < nC; s += 32) {
+        uint32_t i = s + lane;
+        bool ok = false;
+        uint32_t w = 0;
+        if (i < nC) {
+            w = C[i];
+            uint32_t dw = v.deg(w);
+            ok = dw + 1 >= l && merge_count(v.list(w), dw, C, nC, l - 1) + 1 >= l;
+        }
+        unsigned m = __ballot_sync(kFull, ok);
+        if (ok) P[np + __popc(m & ((1u << lane) - 1u))] = (uint16_t)w;
+        np += __popc(m);
+    }
+    return np;
+}
+
+// The subtree below first-level child p0 (C1 = L(p0)), run by one warp.
+template <bool LIST>
+__device__ void ldfs_child(const LView &v, uint32_t p0, const LStack &st, const Emit &em,
+                           DevResult *res, unsigned long long &cnt, unsigned long long &cks) {
+    const unsigned lane = lane_id();
+    const uint32_t k = v.k, cap = st.cap;
+    const uint16_t *C1 = v.list(p0);
+    const uint32_t n1 = v.deg(p0);
+    if (lane == 0) { st.path[1] = p0; st.csize[1] = n1; }
+    __syncwarp();
+    if (k - 2 == 2) {
+        lleaf<LIST>(v, C1, n1, 0, n1, 1, st, em, res, cnt, cks);
+        __syncwarp();
+        return;
+    }
+    uint32_t np = lexpand(v, C1, n1, k - 2, st.pend);
+    if (lane == 0) { st.npend[1] = np; st.ppos[1] = 0; }
+    __syncwarp();
+    int depth = 1;
+    while (depth >= 1) {
+        const uint32_t pp = st.ppos[depth];
+        if (pp >= st.npend[depth]) { depth--; continue; }
+        const uint32_t w = st.pend[(depth - 1) * cap + pp];
+        __syncwarp();
+        if (lane == 0) { st.ppos[depth] = pp + 1; st.path[depth + 1] = w; }
+        const uint16_t *C = depth == 1 ? C1 : st.clist + (depth - 2) * cap;
+        uint16_t *Cn = st.clist + (depth - 1) * cap;  // list of depth + 1
+        const uint32_t nn = warp_intersect16(v.list(w), v.deg(w), C, st.csize[depth], Cn);
+        if (lane == 0) st.csize[depth + 1] = nn;
+        __syncwarp();
+        const uint32_t l = k - 2 - (uint32_t)depth;  // level of the child
+        if (l == 2) {
+            lleaf<LIST>(v, Cn, nn, 0, nn, depth + 1, st, em, res, cnt, cks);
+            __syncwarp();
+        } else if (nn + 1 >= l) {
+            uint32_t np2 = lexpand(v, Cn, nn, l, st.pend + depth * cap);
+            if (lane == 0) { st.npend[depth + 1] = np2; st.ppos[depth + 1] = 0; }
+            __syncwarp();
+            depth++;
+        }
+    }
+}
+
+// Warp per root (d+ <= 128): single-pass build (rows kept in stream order)
+// and the root's children in turn.
 template <bool LIST>
 __device__ void sdegree_root_local(uint32_t u, uint32_t k, uint32_t D, const uint32_t *__restrict__ optr,
                                    const uint32_t *__restrict__ oadj, uint32_t *S, const Emit &em,
@@ -288,13 +471,7 @@ __device__ void sdegree_root_local(uint32_t u, uint32_t k, uint32_t D, const uin
     uint32_t *hk = S + L.HK;
     uint16_t *hv = reinterpret_cast<uint16_t *>(S + L.HV);
     uint16_t *ladj = reinterpret_cast<uint16_t *>(S + L.LADJ);
-    uint16_t *clist = reinterpret_cast<uint16_t *>(S + L.CL);   // depth t >= 1 at (t-1)*D
-    uint16_t *pend = reinterpret_cast<uint16_t *>(S + L.PD);    // depth t at t*D
-    uint32_t *csize = S + L.META;
-    uint32_t *npend = csize + k;
-    uint32_t *ppos = npend + k;
-    uint32_t *path = ppos + k;
-    uint32_t *sortedR = S + L.SORTED;
+    const LStack st = stack_ptrs(S + L.STACK, D, k);
 
     const uint32_t base = optr[u];
     const uint32_t d = optr[u + 1] - base;
@@ -323,7 +500,7 @@ __device__ void sdegree_root_local(uint32_t u, uint32_t k, uint32_t D, const uin
     const uint32_t total = running;
     const uint32_t lo_id = nbr[0], hi_id = nbr[d - 1];
 
-    // ---- reduced out-lists L(i): the members' out-lists are streamed as one
+    // reduced out-lists L(i): the members' out-lists are streamed as one
     // flattened sequence; matches (hash probe into N+_u) are ballot-compacted
     // in stream order, so each L(i) is contiguous and ascending.
     uint32_t T, hshift;
@@ -365,156 +542,265 @@ __device__ void sdegree_root_local(uint32_t u, uint32_t k, uint32_t D, const uin
     }
     __syncwarp();
 
-    auto ldeg = [&](uint32_t i) -> uint32_t { return lofs[i + 1] - lofs[i]; };
-    auto Lp = [&](uint32_t i) -> const uint16_t * { return ladj + lofs[i]; };
-
-    // leaf (l = 2): every w in C closes |L(w) intersect C| cliques
-    auto leaf = [&](const uint16_t *C, uint32_t nC, uint32_t depth) {
-        if (LIST && lane == 0) {
-            sortedR[0] = u;
-            for (uint32_t t = 1; t <= depth; t++) {
-                uint32_t x = nbr[path[t]], j = t;
-                while (j > 0 && sortedR[j - 1] > x) { sortedR[j] = sortedR[j - 1]; j--; }
-                sortedR[j] = x;
-            }
+    const LView v{nbr, lofs, ladj, d, u, k};
+    if (k == 3) {
+        // C = all of N+_u: every edge of the reduced DAG closes a triangle
+        if (!LIST) {
+            if (lane == 0) cnt += lofs[d];
+            return;
         }
-        if (LIST) __syncwarp();
-        for (uint32_t s = 0; s < nC; s += 32) {
-            uint32_t i = s + lane;
-            uint32_t x = 0, w = 0;
-            if (i < nC) {
-                w = C[i];
-                uint32_t dw = ldeg(w);
-                if (dw) x = merge_count(Lp(w), dw, C, nC, 0xFFFFFFFFu);
-            }
-            cnt += x;
-            if (LIST) {
-                // slots for this batch of lanes, then each lane re-merges and emits
+        for (uint32_t i = lane; i < d; i += 32) st.clist[i] = (uint16_t)i;
+        __syncwarp();
+        lleaf<LIST>(v, st.clist, d, 0, d, 0, st, em, res, cnt, cks);
+        return;
+    }
+    // depth 0: C = all local indices, so |L(w) intersect C| = |L(w)|
+    for (uint32_t w = 0; w < d; w++)
+        if (v.deg(w) + 2 >= k) ldfs_child<LIST>(v, w, st, em, res, cnt, cks);
+}
+
+// ------------------------------------------------ CTA per root (d+ > 128)
+// Shared region (words) of the CTA form; the reduced lists and the per-warp
+// stacks follow it in shared memory (lists move to the global arena when
+// they do not leave room for enough warps).
+struct CLay {
+    uint32_t D, WPD, NBR, RS, PRE, LOFS, HK, HV, P0, META, total;
+};
+
+__host__ __device__ inline CLay make_clayout(uint32_t D) {
+    CLay L;
+    L.D = D;
+    uint32_t w = D / 32;
+    L.WPD = (w & 1) ? w : w + 1;
+    L.NBR = 0;
+    L.RS = L.NBR + D;
+    L.PRE = L.RS + D;          // D + 1
+    L.LOFS = L.PRE + D + 1;    // D + 1
+    L.HK = L.LOFS + D + 1;     // 2D
+    L.HV = L.HK + 2 * D;       // 2D u16
+    L.P0 = L.HV + D;           // D u16: first-level children
+    L.META = L.P0 + D / 2;     // 16 words
+    L.total = (L.META + 16 + 3) & ~3u;
+    return L;
+}
+
+// arena slice per CTA: directed bit-rows (D x WPD words) + reduced lists
+__host__ __device__ inline size_t cta_arena_words(uint32_t D) {
+    CLay L = make_clayout(D);
+    return (size_t)D * L.WPD + ((size_t)D * (D - 1) / 2 + 1) / 2 + 4;
+}
+
+template <bool LIST>
+__global__ void __launch_bounds__(512) k_sdegree_cta(uint32_t k, uint32_t D, const uint32_t *__restrict__ optr,
+                                                    const uint32_t *__restrict__ oadj,
+                                                    const uint32_t *__restrict__ roots, uint32_t begin,
+                                                    uint32_t end, unsigned *queue, uint32_t *arena,
+                                                    uint32_t smem_words, Emit em,
+                                                    unsigned long long *per_root, DevResult *res) {
+    extern __shared__ uint32_t smem[];
+    const CLay L = make_clayout(D);
+    const uint32_t tid = threadIdx.x, nth = blockDim.x, lane = lane_id(), warp = tid >> 5;
+    const uint32_t nwarps = nth >> 5;
+    uint32_t *nbr = smem + L.NBR;
+    uint32_t *rs = smem + L.RS;
+    uint32_t *pre = smem + L.PRE;
+    uint32_t *lofs = smem + L.LOFS;
+    uint32_t *hk = smem + L.HK;
+    uint16_t *hv = reinterpret_cast<uint16_t *>(smem + L.HV);
+    uint16_t *p0 = reinterpret_cast<uint16_t *>(smem + L.P0);
+    uint32_t *meta = smem + L.META;
+    uint32_t *slice = arena + (size_t)blockIdx.x * cta_arena_words(D);
+    uint32_t *bits = slice;
+    uint16_t *ladj_g = reinterpret_cast<uint16_t *>(slice + (size_t)D * L.WPD);
+    unsigned long long cnt = 0, cks = 0;
+    for (;;) {
+        if (tid == 0) meta[15] = atomicAdd(queue, 1u);
+        __syncthreads();
+        const uint32_t idx = meta[15];
+        if (idx >= end - begin) break;
+        const uint32_t u = roots[begin + idx];
+        const uint32_t base = optr[u], d = optr[u + 1] - base;
+        const unsigned long long before = cnt;
+
+        // ---- build: members, out-list lengths, hash of N+_u, zero bit-rows
+        for (uint32_t i = tid; i < d; i += nth) {
+            uint32_t x = oadj[base + i];
+            nbr[i] = x;
+            uint32_t r0 = optr[x];
+            rs[i] = r0;
+            pre[i] = optr[x + 1] - r0;
+        }
+        uint32_t T, hshift;
+        hash_size(d, &T, &hshift);
+        for (uint32_t i = tid; i < T; i += nth) hk[i] = kHashEmpty;
+        for (uint32_t i = tid; i < d * L.WPD; i += nth) bits[i] = 0;
+        if (tid < 15) meta[tid] = 0;  // meta[15] holds the root index
+        __syncthreads();
+        if (warp == 0) {
+            uint32_t running = 0;
+            for (uint32_t c0 = 0; c0 < d; c0 += 32) {
+                uint32_t i = c0 + lane;
+                uint32_t x = i < d ? pre[i] : 0;
                 uint32_t incl = x;
 #pragma unroll
                 for (int o = 1; o < 32; o <<= 1) {
                     uint32_t y = __shfl_up_sync(kFull, incl, o);
                     if (lane >= (unsigned)o) incl += y;
                 }
-                uint32_t tot = __shfl_sync(kFull, incl, 31);
-                unsigned long long slot0 = 0;
-                if (tot && em.ring) {
-                    if (lane == 0) slot0 = atomicAdd(&res->emitted, (unsigned long long)tot);
-                    slot0 = __shfl_sync(kFull, slot0, 0);
+                if (i < d) pre[i] = running + incl - x;
+                running += __shfl_sync(kFull, incl, 31);
+            }
+            if (lane == 0) pre[d] = running;
+        }
+        for (uint32_t i = tid; i < d; i += nth) {
+            uint32_t key = nbr[i], h = hash_slot(key, hshift);
+            while (atomicCAS(&hk[h], kHashEmpty, key) != kHashEmpty) h = (h + 1) & (T - 1);
+            hv[h] = (uint16_t)i;
+        }
+        __syncthreads();
+        // ---- directed bit-rows: bit j of row i iff member j is in N+_{v_i}
+        const uint32_t total = pre[d];
+        const uint32_t lo_id = nbr[0], hi_id = nbr[d - 1];
+        uint32_t a0 = 0;
+        for (uint32_t c = warp * 32; c < total; c += nth) {
+            uint32_t lo = a0, hi = d;
+            while (hi - lo > 1) {
+                uint32_t m = (lo + hi) >> 1;
+                if (pre[m] <= c) lo = m; else hi = m;
+            }
+            a0 = lo;
+            const uint32_t e = c + lane;
+            if (e < total) {
+                uint32_t a = a0;
+                while (pre[a + 1] <= e) a++;
+                uint32_t x = oadj[rs[a] + (e - pre[a])];
+                if (x >= lo_id && x <= hi_id) {
+                    int j = hash_find(hk, hv, T, hshift, x);
+                    if (j >= 0) atomicOr(&bits[a * L.WPD + ((uint32_t)j >> 5)], 1u << (j & 31));
                 }
-                if (x) {
-                    unsigned long long slot = slot0 + (incl - x);
-                    const uint16_t *a = Lp(w);
-                    uint32_t na = ldeg(w), ia = 0, ib = 0;
-                    uint32_t vid = nbr[w];
-                    while (ia < na && ib < nC) {
-                        uint32_t p = a[ia], q = C[ib];
-                        if (p == q) {
-                            uint32_t b2 = nbr[p];
-                            uint32_t e0 = vid < b2 ? vid : b2, e1 = vid < b2 ? b2 : vid;
-                            uint32_t ex[2] = {e0, e1};
-                            uint32_t rec[KCL_MAX_K];
-                            uint32_t nr = k - 2, ri = 0, ei = 0, o = 0;
-                            while (ri < nr || ei < 2) {
-                                uint32_t r = ri < nr ? sortedR[ri] : 0xFFFFFFFFu;
-                                if (ei < 2 && ex[ei] < r) rec[o++] = ex[ei++];
-                                else rec[o++] = sortedR[ri++];
-                            }
-                            uint64_t h = hash_seed(k);
-                            for (uint32_t z = 0; z < k; z++) h = mix64(h ^ (uint64_t)rec[z]);
-                            cks += h;
-                            if (em.ring) {
-                                unsigned long long sl = slot;
-                                bool ok = true;
-                                if (em.wrap) sl %= em.capacity;
-                                else ok = sl < em.capacity;
-                                if (ok)
-                                    for (uint32_t z = 0; z < k; z++) em.ring[sl * k + z] = rec[z];
-                            }
-                            slot++;
-                        }
-                        ia += p <= q;
-                        ib += q <= p;
+            }
+        }
+        __syncthreads();
+        // ---- row lengths, longest row, offsets
+        for (uint32_t i = tid; i < d; i += nth) {
+            uint32_t c = 0;
+            for (uint32_t t = 0; t < L.WPD; t++) c += __popc(bits[i * L.WPD + t]);
+            lofs[i] = c;
+            atomicMax(&meta[3], c);
+        }
+        __syncthreads();
+        if (warp == 0) {
+            uint32_t running = 0;
+            for (uint32_t c0 = 0; c0 <= d; c0 += 32) {
+                uint32_t i = c0 + lane;
+                uint32_t x = i < d ? lofs[i] : 0;
+                uint32_t incl = x;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    uint32_t y = __shfl_up_sync(kFull, incl, o);
+                    if (lane >= (unsigned)o) incl += y;
+                }
+                if (i <= d) lofs[i] = running + incl - x;
+                running += __shfl_sync(kFull, incl, 31);
+            }
+            if (lane == 0) {
+                // place the lists and size the stacks: lists in shared memory
+                // unless that would leave fewer than min(8, possible) warps
+                uint32_t cap = meta[3] ? meta[3] : 1;
+                uint32_t sw = stack_words(cap, k);
+                uint32_t budget = smem_words - L.total;
+                uint32_t lw = (lofs[d] + 1) / 2;
+                lw = (lw + 3) & ~3u;
+                uint32_t nw_g = budget / sw;
+                if (nw_g > nwarps) nw_g = nwarps;
+                uint32_t nw_s = lw <= budget ? (budget - lw) / sw : 0;
+                if (nw_s > nwarps) nw_s = nwarps;
+                uint32_t want = nw_g < 8 ? nw_g : 8;
+                bool in_smem = nw_s >= 1 && nw_s >= want;
+                meta[4] = in_smem ? 1u : 0u;
+                meta[5] = in_smem ? nw_s : nw_g;
+                meta[6] = sw;
+                meta[7] = in_smem ? lw : 0u;  // stacks start after the lists
+            }
+        }
+        __syncthreads();
+        uint16_t *ladj = meta[4] ? reinterpret_cast<uint16_t *>(smem + L.total) : ladj_g;
+        // ---- extraction: row i's bits in ascending order -> L(i)
+        for (uint32_t i = tid; i < d; i += nth) {
+            uint32_t o = lofs[i];
+            for (uint32_t t = 0; t < L.WPD; t++) {
+                uint32_t m = bits[i * L.WPD + t];
+                while (m) {
+                    ladj[o++] = (uint16_t)(t * 32 + (__ffs(m) - 1));
+                    m &= m - 1;
+                }
+            }
+        }
+        const uint32_t nw_dfs = meta[5], sw = meta[6];
+        if (nw_dfs == 0 && tid == 0) atomicOr(&res->status, DEV_ERR_INTERNAL);  // no stack fits
+        const LView v{nbr, lofs, ladj, d, u, k};
+        const uint32_t cap = meta[3] ? meta[3] : 1;
+        // ---- first-level children (|L(w)| >= k-2), longest lists first
+        if (k > 3 && warp == 0) {
+            // four passes: |L(w)| in [3/4, inf), [1/2, 3/4), [1/4, 1/2), [0, 1/4) of the longest
+            uint32_t n0 = 0, mx = meta[3];
+            for (int bucket = 3; bucket >= 0; bucket--) {
+                uint32_t lo = bucket == 0 ? 0u : (mx * (uint32_t)bucket) / 4;
+                uint32_t hi = bucket == 3 ? 0xFFFFFFFFu : (mx * (uint32_t)(bucket + 1)) / 4;
+                for (uint32_t s = 0; s < d; s += 32) {
+                    uint32_t w = s + lane;
+                    bool ok = false;
+                    if (w < d) {
+                        uint32_t dw = lofs[w + 1] - lofs[w];
+                        ok = dw + 2 >= k && dw >= lo && dw < hi;
                     }
+                    unsigned m = __ballot_sync(kFull, ok);
+                    if (ok) p0[n0 + __popc(m & ((1u << lane) - 1u))] = (uint16_t)w;
+                    n0 += __popc(m);
+                }
+            }
+            if (lane == 0) { meta[8] = n0; meta[9] = 0; }
+        }
+        if (k == 3 && LIST) {
+            for (uint32_t i = tid; i < d; i += nth) p0[i] = (uint16_t)i;
+        }
+        __syncthreads();
+        if (warp < nw_dfs) {
+            const LStack st = stack_ptrs(smem + L.total + meta[7] + warp * sw, cap < d ? cap : d, k);
+            if (k == 3) {
+                if (!LIST) {
+                    if (tid == 0) cnt += lofs[d];
+                } else {
+                    // identity candidate list, split across the DFS warps
+                    uint32_t chunk = (d + nw_dfs - 1) / nw_dfs;
+                    uint32_t b0 = warp * chunk, b1 = b0 + chunk < d ? b0 + chunk : d;
+                    if (b0 < b1) lleaf<LIST>(v, p0, d, b0, b1, 0, st, em, res, cnt, cks);
+                }
+            } else {
+                const uint32_t n0 = meta[8];
+                for (;;) {
+                    uint32_t i = 0;
+                    if (lane == 0) i = atomicAdd(&meta[9], 1u);
+                    i = __shfl_sync(kFull, i, 0);
+                    if (i >= n0) break;
+                    ldfs_child<LIST>(v, p0[i], st, em, res, cnt, cks);
                 }
             }
         }
-    };
-    // inner node at level l: pending children w with |L(w) intersect C| >= l-1
-    auto expand = [&](const uint16_t *C, uint32_t nC, uint32_t l, uint16_t *P) -> uint32_t {
-        uint32_t np = 0;
-        for (uint32_t s = 0; s < nC; s += 32) {
-            uint32_t i = s + lane;
-            bool ok = false;
-            uint32_t w = 0;
-            if (i < nC) {
-                w = C[i];
-                uint32_t dw = ldeg(w);
-                ok = dw + 1 >= l && merge_count(Lp(w), dw, C, nC, l - 1) + 1 >= l;
-            }
-            unsigned m = __ballot_sync(kFull, ok);
-            if (ok) P[np + __popc(m & ((1u << lane) - 1u))] = (uint16_t)w;
-            np += __popc(m);
+        if (per_root) {
+            unsigned long long mine = cnt - before;
+            for (int o = 16; o > 0; o >>= 1) mine += __shfl_down_sync(kFull, mine, o);
+            if (lane == 0 && mine) atomicAdd(&per_root[u], mine);
         }
-        return np;
-    };
-
-    const uint32_t l0 = k - 1;
-    if (l0 == 2) {
-        // C = all of N+_u: every edge of the reduced DAG closes a triangle
-        if (!LIST) {
-            if (lane == 0) cnt += lofs[d];
-            return;
-        }
-        // listing: C is the identity list 0..d-1 (built in clist)
-        for (uint32_t i = lane; i < d; i += 32) clist[i] = (uint16_t)i;
-        __syncwarp();
-        leaf(clist, d, 0);
-        return;
+        __syncthreads();
     }
-    // depth 0: C = all local indices, so |L(w) intersect C| = |L(w)|
-    {
-        uint32_t np = 0;
-        for (uint32_t s = 0; s < d; s += 32) {
-            uint32_t w = s + lane;
-            bool ok = w < d && ldeg(w) + 1 >= l0;
-            unsigned m = __ballot_sync(kFull, ok);
-            if (ok) pend[np + __popc(m & ((1u << lane) - 1u))] = (uint16_t)w;
-            np += __popc(m);
-        }
-        if (lane == 0) { npend[0] = np; ppos[0] = 0; path[0] = 0; }
-        __syncwarp();
+    for (int o = 16; o > 0; o >>= 1) {
+        cnt += __shfl_down_sync(kFull, cnt, o);
+        cks += __shfl_down_sync(kFull, cks, o);
     }
-    int depth = 0;
-    while (depth >= 0) {
-        const uint32_t pp = ppos[depth];
-        if (pp >= npend[depth]) { depth--; continue; }
-        const uint32_t v = pend[depth * D + pp];
-        __syncwarp();
-        if (lane == 0) { ppos[depth] = pp + 1; path[depth + 1] = v; }
-        // child candidate list C' = L(v) intersect C
-        uint16_t *Cn = clist + depth * D;  // list of depth + 1
-        uint32_t nn;
-        if (depth == 0) {
-            nn = ldeg(v);
-            const uint16_t *a = Lp(v);
-            for (uint32_t i = lane; i < nn; i += 32) Cn[i] = a[i];
-        } else {
-            const uint16_t *C = clist + (depth - 1) * D;
-            nn = warp_intersect16(Lp(v), ldeg(v), C, csize[depth], Cn);
-        }
-        if (lane == 0) csize[depth + 1] = nn;
-        __syncwarp();
-        const uint32_t l = k - 2 - (uint32_t)depth;  // level of the child
-        if (l == 2) {
-            leaf(Cn, nn, depth + 1);
-            __syncwarp();
-        } else if (nn + 1 >= l) {
-            uint32_t np = expand(Cn, nn, l, pend + (depth + 1) * D);
-            if (lane == 0) { npend[depth + 1] = np; ppos[depth + 1] = 0; }
-            __syncwarp();
-            depth++;
-        }
+    if (lane == 0) {
+        add_count(&res->count, &res->count_carry, cnt);
+        if (LIST && cks) atomicAdd(&res->checksum, cks);
     }
 }
 
@@ -557,29 +843,65 @@ __global__ void __launch_bounds__(128) k_sdegree(uint32_t k, uint32_t D, const u
     }
 }
 
-// Out-degree classes.  Up to 1024: reduced lists (shared memory up to 128,
-// a global arena above); beyond: SDegreeList on the global out-lists.
+// Out-degree classes: <= 128 warp per root (reduced lists, shared memory);
+// <= 1024 CTA per root (reduced lists); above, SDegreeList on the global
+// out-lists with a warp per root and its stack in a global arena.
 constexpr uint32_t kClassD[] = {32, 64, 128, 256, 512, 1024, 4096, 16384, 65536};
 constexpr int kNumClasses = 9;
-constexpr int kSmemClasses = 3;
-constexpr int kLocalClasses = 6;
+constexpr int kWarpClasses = 3;
+constexpr int kCtaClasses = 6;
 constexpr size_t kSmemPerBlock = 96 * 1024;
 
-uint32_t class_words(int c, uint32_t k) {
-    return c < kLocalClasses ? make_llayout(kClassD[c], k).total : make_slayout(kClassD[c], k).total;
-}
+size_t cta_smem_bytes(uint32_t D) { return D <= 256 ? 100 * 1024 : 200 * 1024; }
 
-int arena_warps(int c, int num_sms) { return num_sms * (c < kLocalClasses ? 4 : 2); }
-
-template <bool LIST, bool GLOBAL, bool LOCAL>
-void launch_one(uint32_t k, uint32_t D, uint32_t words, Workspace &w, uint32_t begin, uint32_t end,
-                unsigned *queue, const Emit &em, unsigned long long *per_root, int wpb, int blocks,
-                cudaStream_t s) {
-    size_t smem = GLOBAL ? 0 : (size_t)wpb * words * sizeof(uint32_t);
-    auto kern = k_sdegree<LIST, GLOBAL, LOCAL>;
-    if (!GLOBAL) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+template <bool LIST>
+void launch_warp_local(uint32_t k, uint32_t D, Workspace &w, uint32_t begin, uint32_t end,
+                       unsigned *queue, const Emit &em, unsigned long long *per_root, int num_sms,
+                       cudaStream_t s) {
+    uint32_t words = make_llayout(D, k).total;
+    int wpb = (int)(kSmemPerBlock / ((size_t)words * 4));
+    if (wpb > 4) wpb = 4;
+    if (wpb < 1) wpb = 1;
+    size_t smem = (size_t)wpb * words * 4;
+    auto kern = k_sdegree<LIST, false, true>;
+    int occ = 0;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, wpb * 32, smem) != cudaSuccess)
+        (void)cudaGetLastError();
+    if (occ < 1) occ = 1;
+    uint32_t blocks = (uint32_t)num_sms * occ;
+    uint32_t need = (end - begin + wpb - 1) / wpb;
+    if (blocks > need) blocks = need;
     kern<<<blocks, wpb * 32, smem, s>>>(k, D, w.optr, w.oadj, w.roots, begin, end, queue, w.arena,
                                         words, em, per_root, w.res);
+}
+
+template <bool LIST>
+void launch_cta(uint32_t k, uint32_t D, Workspace &w, uint32_t begin, uint32_t end, unsigned *queue,
+                const Emit &em, unsigned long long *per_root, int num_sms, cudaStream_t s) {
+    size_t smem = cta_smem_bytes(D);
+    auto kern = k_sdegree_cta<LIST>;
+    int occ = 0;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, 512, smem) != cudaSuccess)
+        (void)cudaGetLastError();
+    if (occ < 1) occ = 1;
+    if (occ > 2) occ = 2;
+    uint32_t blocks = (uint32_t)num_sms * occ;
+    if (blocks > end - begin) blocks = end - begin;
+    kern<<<blocks, 512, smem, s>>>(k, D, w.optr, w.oadj, w.roots, begin, end, queue, w.arena,
+                                   (uint32_t)(smem / 4), em, per_root, w.res);
+}
+
+template <bool LIST>
+void launch_global_lists(uint32_t k, uint32_t D, Workspace &w, uint32_t begin, uint32_t end,
+                         unsigned *queue, const Emit &em, unsigned long long *per_root, int num_sms,
+                         cudaStream_t s) {
+    uint32_t words = make_slayout(D, k).total;
+    uint32_t blocks = (uint32_t)num_sms;
+    if (blocks * 2 > end - begin) blocks = (end - begin + 1) / 2;
+    k_sdegree<LIST, true, false><<<blocks, 64, 0, s>>>(k, D, w.optr, w.oadj, w.roots, begin, end,
+                                                       queue, w.arena, words, em, per_root, w.res);
 }
 
 }  // namespace
@@ -592,9 +914,10 @@ int sdegree_classes(uint32_t *limits, int max) {
 
 size_t sdegree_arena_words(uint32_t k, int num_sms, uint32_t max_outdeg) {
     size_t need = 0;
-    for (int c = kSmemClasses; c < kNumClasses; c++) {
+    for (int c = kWarpClasses; c < kNumClasses; c++) {
         if (kClassD[c - 1] >= max_outdeg) break;
-        size_t words = (size_t)arena_warps(c, num_sms) * class_words(c, k);
+        size_t words = c < kCtaClasses ? (size_t)num_sms * 2 * cta_arena_words(kClassD[c])
+                                       : (size_t)num_sms * 2 * make_slayout(kClassD[c], k).total;
         if (words > need) need = words;
     }
     return need;
@@ -611,31 +934,16 @@ int launch_sdegree(const kcl_graph *g, uint32_t k, Workspace &w, const uint32_t 
         if (end <= begin) continue;
         uint32_t D = kClassD[c];
         unsigned *q = w.queue + c;
-        uint32_t nroots = end - begin;
-        uint32_t words = class_words(c, k);
-        bool global = c >= kSmemClasses;
-        int wpb, blocks;
-        if (global) {
-            wpb = c < kLocalClasses ? 4 : 2;
-            blocks = g->num_sms;
+        if (c < kWarpClasses) {
+            if (la.listing) launch_warp_local<true>(k, D, w, begin, end, q, em, la.per_root, g->num_sms, s);
+            else launch_warp_local<false>(k, D, w, begin, end, q, em, la.per_root, g->num_sms, s);
+        } else if (c < kCtaClasses) {
+            if (la.listing) launch_cta<true>(k, D, w, begin, end, q, em, la.per_root, g->num_sms, s);
+            else launch_cta<false>(k, D, w, begin, end, q, em, la.per_root, g->num_sms, s);
         } else {
-            wpb = (int)(kSmemPerBlock / ((size_t)words * 4));
-            if (wpb > 4) wpb = 4;
-            if (wpb < 1) wpb = 1;
-            blocks = g->num_sms * (D <= 64 ? 8 : 4);
+            if (la.listing) launch_global_lists<true>(k, D, w, begin, end, q, em, la.per_root, g->num_sms, s);
+            else launch_global_lists<false>(k, D, w, begin, end, q, em, la.per_root, g->num_sms, s);
         }
-        uint32_t need = (nroots + wpb - 1) / wpb;
-        if ((uint32_t)blocks > need) blocks = (int)need;
-#define KCL_SD(LST, GLB, LOC) \
-    launch_one<LST, GLB, LOC>(k, D, words, w, begin, end, q, em, la.per_root, wpb, blocks, s)
-        if (!global) {
-            if (la.listing) KCL_SD(true, false, true); else KCL_SD(false, false, true);
-        } else if (c < kLocalClasses) {
-            if (la.listing) KCL_SD(true, true, true); else KCL_SD(false, true, true);
-        } else {
-            if (la.listing) KCL_SD(true, true, false); else KCL_SD(false, true, false);
-        }
-#undef KCL_SD
         launches++;
     }
     return launches;
