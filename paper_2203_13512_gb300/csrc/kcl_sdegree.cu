@@ -197,8 +197,8 @@ __device__ void sdegree_root(uint32_t u, uint32_t k, uint32_t D, const uint32_t 
 // ascending id order; L(i) = N+_{v_i} intersect N+_u as a sorted list of local
 // indices.  The DFS then intersects short sorted lists:
 //   - lanes evaluate the candidates of a node in parallel, each merging its
-//     L(w) with C (two-pointer merge join, stopping early once the size
-//     bound is met);
+//     L(w) with C (block merge join, 4 x 4 compares per step, stopping early
+//     once the size bound is met);
 //   - the chosen child's C' = L(v) intersect C is materialised warp-
 //     cooperatively (lanes stream the shorter list, binary-search the other,
 //     ballot-compact the matches in order).
@@ -208,43 +208,70 @@ __device__ void sdegree_root(uint32_t u, uint32_t k, uint32_t D, const uint32_t 
 // larger ones one CTA each: the CTA builds the lists once and deals the
 // root's first-level children to its warps.
 
-// Warp-per-root layout (words): build scratch, lists, one DFS stack with
-// list capacity D.
-struct LLay {
-    uint32_t D, NBR, LOFS, PRE, RS, HK, HV, LADJ, STACK, total;
-};
+// Every reduced list is stored from an 8-byte boundary and padded with
+// 0xFFFF to a multiple of 4 entries, so the merge join can take the paper's
+// SIMD form (Section VI-C, Example 5): load a block of 4 entries from each
+// list, compare all 16 pairs (__vcmpeq2 on packed halves), and advance the
+// block whose last entry is smaller (both when equal).
+
+constexpr uint16_t kPad = 0xFFFF;  // above every local index (< 1024)
+
+__host__ __device__ inline uint32_t round4(uint32_t x) { return (x + 3) & ~3u; }
 
 __host__ __device__ inline uint32_t stack_words(uint32_t cap, uint32_t k) {
-    // clist and pend: (k-2) lists of `cap` u16 each; csize, npend, ppos,
-    // path: k words each; sortedR: 32 words
-    return (2 * (((k - 2) * cap + 1) / 2) + 4 * k + 32 + 3) & ~3u;
+    // clist and pend: (k-2) lists of round4(cap) u16 each; csize, npend,
+    // ppos, path: k words each; sortedR: 32 words
+    return (2 * ((k - 2) * round4(cap) / 2) + 4 * k + 32 + 3) & ~3u;
 }
+
+// Warp-per-root layout (words): build scratch, directed bit-rows, lists, one
+// DFS stack with list capacity D.
+struct LLay {
+    uint32_t D, WPD, NBR, LOFS, PRE, RS, HK, HV, LEN, BITS, LADJ, STACK, total;
+};
 
 __host__ __device__ inline LLay make_llayout(uint32_t D, uint32_t k) {
     LLay L;
     L.D = D;
-    uint64_t emax = (uint64_t)D * (D - 1) / 2;
+    uint32_t w = D / 32;
+    L.WPD = (w & 1) ? w : w + 1;
+    uint64_t emax = (uint64_t)D * (D - 1) / 2 + 3 * (uint64_t)D;  // padded lists
     L.NBR = 0;
     L.LOFS = D;
     L.PRE = L.LOFS + D + 1;   // prefix sums of the members' out-degrees
     L.RS = L.PRE + D + 1;     // row starts of the members' out-lists
     L.HK = L.RS + D;          // hash keys (2D)
     L.HV = L.HK + 2 * D;      // hash values, u16 (2D)
-    L.LADJ = L.HV + D;
-    L.STACK = L.LADJ + (uint32_t)((emax + 1) / 2);
+    L.LEN = L.HV + D;         // list lengths, u16 (D)
+    L.BITS = L.LEN + D / 2;   // directed bit-rows (D x WPD)
+    L.LADJ = (L.BITS + D * L.WPD + 3) & ~3u;
+    L.STACK = (L.LADJ + (uint32_t)((emax + 1) / 2) + 3) & ~3u;
     L.total = (L.STACK + stack_words(D, k) + 3) & ~3u;
     return L;
 }
 
-// |a intersect b| for sorted u16 lists, stopping once `stop` is reached.
-__device__ __forceinline__ uint32_t merge_count(const uint16_t *a, uint32_t na, const uint16_t *b,
-                                                uint32_t nb, uint32_t stop) {
+// |a intersect b| for padded u16 lists (8-byte aligned, lengths na, nb),
+// block form: 4 x 4 all-pairs compares per step; stops once `stop` is met.
+__device__ __forceinline__ uint32_t merge_count4(const uint16_t *a, uint32_t na, const uint16_t *b,
+                                                 uint32_t nb, uint32_t stop) {
+    const uint2 *A = reinterpret_cast<const uint2 *>(a);
+    const uint2 *B = reinterpret_cast<const uint2 *>(b);
+    const uint32_t na4 = (na + 3) >> 2, nb4 = (nb + 3) >> 2;
     uint32_t i = 0, j = 0, c = 0;
-    while (i < na && j < nb && c < stop) {
-        uint32_t x = a[i], y = b[j];
-        c += x == y;
-        i += x <= y;
-        j += y <= x;
+    while (i < na4 && j < nb4 && c < stop) {
+        const uint2 x = A[i], y = B[j];
+        const uint32_t y0 = y.x, y1 = y.y;
+        const uint32_t y0r = __byte_perm(y0, 0, 0x1032), y1r = __byte_perm(y1, 0, 0x1032);
+        // a padding entry never counts (it may meet padding in b)
+        const uint32_t v0 = ~__vcmpeq2(x.x, 0xFFFFFFFFu), v1 = ~__vcmpeq2(x.y, 0xFFFFFFFFu);
+        uint32_t m0 = (__vcmpeq2(x.x, y0) | __vcmpeq2(x.x, y0r) | __vcmpeq2(x.x, y1) |
+                       __vcmpeq2(x.x, y1r)) & v0;
+        uint32_t m1 = (__vcmpeq2(x.y, y0) | __vcmpeq2(x.y, y0r) | __vcmpeq2(x.y, y1) |
+                       __vcmpeq2(x.y, y1r)) & v1;
+        c += (__popc(m0) + __popc(m1)) >> 4;
+        const uint32_t amax = x.y >> 16, bmax = y1 >> 16;
+        i += amax <= bmax;
+        j += bmax <= amax;
     }
     return c;
 }
@@ -258,7 +285,8 @@ __device__ __forceinline__ bool contains16(const uint16_t *a, uint32_t n, uint32
     return lo < n && a[lo] == x;
 }
 
-// Warp-cooperative C' = a intersect b (sorted u16 lists) written to out.
+// Warp-cooperative C' = a intersect b (sorted u16 lists) written to out and
+// padded to a multiple of 4 entries.
 __device__ uint32_t warp_intersect16(const uint16_t *a, uint32_t na, const uint16_t *b, uint32_t nb,
                                      uint16_t *out) {
     const unsigned lane = lane_id();
@@ -267,43 +295,46 @@ __device__ uint32_t warp_intersect16(const uint16_t *a, uint32_t na, const uint1
         uint32_t tn = na; na = nb; nb = tn;
     }
     uint32_t nout = 0;
-    if (na == 0) return 0;
-    const uint32_t blo = b[0], bhi = b[nb - 1];
-    for (uint32_t s = 0; s < na; s += 32) {
-        uint32_t i = s + lane;
-        bool f = false;
-        uint32_t x = 0;
-        if (i < na) {
-            x = a[i];
-            f = x >= blo && x <= bhi && contains16(b, nb, x);
+    if (na > 0) {
+        const uint32_t blo = b[0], bhi = b[nb - 1];
+        for (uint32_t s = 0; s < na; s += 32) {
+            uint32_t i = s + lane;
+            bool f = false;
+            uint32_t x = 0;
+            if (i < na) {
+                x = a[i];
+                f = x >= blo && x <= bhi && contains16(b, nb, x);
+            }
+            unsigned m = __ballot_sync(kFull, f);
+            if (f) out[nout + __popc(m & ((1u << lane) - 1u))] = (uint16_t)x;
+            nout += __popc(m);
         }
-        unsigned m = __ballot_sync(kFull, f);
-        if (f) out[nout + __popc(m & ((1u << lane) - 1u))] = (uint16_t)x;
-        nout += __popc(m);
     }
+    if (lane < round4(nout) - nout) out[nout + lane] = kPad;
     return nout;
 }
 
 // A built reduced subproblem and one warp's DFS stack.
 struct LView {
     const uint32_t *nbr;   // local index -> original id
-    const uint32_t *lofs;  // d + 1 offsets into ladj
-    const uint16_t *ladj;  // reduced out-lists, ascending local indices
+    const uint32_t *lofs;  // list offsets (u16 units, multiples of 4)
+    const uint16_t *len;   // list lengths
+    const uint16_t *ladj;  // reduced out-lists, ascending local indices, padded
     uint32_t d, u, k;
-    __device__ __forceinline__ uint32_t deg(uint32_t i) const { return lofs[i + 1] - lofs[i]; }
+    __device__ __forceinline__ uint32_t deg(uint32_t i) const { return len[i]; }
     __device__ __forceinline__ const uint16_t *list(uint32_t i) const { return ladj + lofs[i]; }
 };
 
 struct LStack {
     uint16_t *clist, *pend;  // (k-2) lists of cap entries each
     uint32_t *csize, *npend, *ppos, *path, *sortedR;
-    uint32_t cap;
+    uint32_t cap;            // a multiple of 4
 };
 
 __device__ inline LStack stack_ptrs(uint32_t *S, uint32_t cap, uint32_t k) {
     LStack st;
-    st.cap = cap;
-    uint32_t lw = ((k - 2) * cap + 1) / 2;
+    st.cap = round4(cap);
+    uint32_t lw = (k - 2) * st.cap / 2;
     st.clist = reinterpret_cast<uint16_t *>(S);
     st.pend = reinterpret_cast<uint16_t *>(S + lw);
     st.csize = S + 2 * lw;
@@ -338,7 +369,7 @@ __device__ void lleaf(const LView &v, const uint16_t *C, uint32_t nC, uint32_t b
         if (i < b1) {
             w = C[i];
             uint32_t dw = v.deg(w);
-            if (dw) x = merge_count(v.list(w), dw, C, nC, 0xFFFFFFFFu);
+            if (dw) x = merge_count4(v.list(w), dw, C, nC, 0xFFFFFFFFu);
         }
         cnt += x;
         if (LIST) {
@@ -404,7 +435,7 @@ __device__ uint32_t lexpand(const LView &v, const uint16_t *C, uint32_t nC, uint
         if (i < nC) {
             w = C[i];
             uint32_t dw = v.deg(w);
-            ok = dw + 1 >= l && merge_count(v.list(w), dw, C, nC, l - 1) + 1 >= l;
+            ok = dw + 1 >= l && merge_count4(v.list(w), dw, C, nC, l - 1) + 1 >= l;
         }
         unsigned m = __ballot_sync(kFull, ok);
         if (ok) P[np + __popc(m & ((1u << lane) - 1u))] = (uint16_t)w;
@@ -456,8 +487,8 @@ __device__ void ldfs_child(const LView &v, uint32_t p0, const LStack &st, const 
     }
 }
 
-// Warp per root (d+ <= 128): single-pass build (rows kept in stream order)
-// and the root's children in turn.
+// Warp per root (d+ <= 128): bit-row build in shared memory, padded lists,
+// then the root's children in turn.
 template <bool LIST>
 __device__ void sdegree_root_local(uint32_t u, uint32_t k, uint32_t D, const uint32_t *__restrict__ optr,
                                    const uint32_t *__restrict__ oadj, uint32_t *S, const Emit &em,
@@ -470,6 +501,8 @@ __device__ void sdegree_root_local(uint32_t u, uint32_t k, uint32_t D, const uin
     uint32_t *rs = S + L.RS;
     uint32_t *hk = S + L.HK;
     uint16_t *hv = reinterpret_cast<uint16_t *>(S + L.HV);
+    uint16_t *len = reinterpret_cast<uint16_t *>(S + L.LEN);
+    uint32_t *bits = S + L.BITS;
     uint16_t *ladj = reinterpret_cast<uint16_t *>(S + L.LADJ);
     const LStack st = stack_ptrs(S + L.STACK, D, k);
 
@@ -484,7 +517,6 @@ __device__ void sdegree_root_local(uint32_t u, uint32_t k, uint32_t D, const uin
             uint32_t r0 = optr[v];
             rs[i] = r0;
             x = optr[v + 1] - r0;
-            lofs[i] = 0;
         }
         uint32_t incl = x;
 #pragma unroll
@@ -495,61 +527,75 @@ __device__ void sdegree_root_local(uint32_t u, uint32_t k, uint32_t D, const uin
         if (i < d) pre[i] = running + incl - x;
         running += __shfl_sync(kFull, incl, 31);
     }
-    if (lane == 0) { pre[d] = running; lofs[d] = 0; }
+    for (uint32_t i = lane; i < d * L.WPD; i += 32) bits[i] = 0;
+    if (lane == 0) pre[d] = running;
     __syncwarp();
     const uint32_t total = running;
     const uint32_t lo_id = nbr[0], hi_id = nbr[d - 1];
 
-    // reduced out-lists L(i): the members' out-lists are streamed as one
-    // flattened sequence; matches (hash probe into N+_u) are ballot-compacted
-    // in stream order, so each L(i) is contiguous and ascending.
+    // directed bit-rows: the members' out-lists are streamed as one flattened
+    // sequence; a hash probe into N+_u finds the local index of each entry
     uint32_t T, hshift;
     hash_size(d, &T, &hshift);
     warp_hash_build(nbr, d, hk, hv, T, hshift);
-    uint32_t run = 0, a0 = 0;
+    uint32_t a0 = 0;
     for (uint32_t c = 0; c < total; c += 32) {
         const uint32_t e = c + lane;
         uint32_t a = a0;
-        int j = -1;
         if (e < total) {
             while (pre[a + 1] <= e) a++;
             uint32_t x = oadj[rs[a] + (e - pre[a])];
-            if (x >= lo_id && x <= hi_id) j = hash_find(hk, hv, T, hshift, x);
+            if (x >= lo_id && x <= hi_id) {
+                int j = hash_find(hk, hv, T, hshift, x);
+                if (j >= 0) atomicOr(&bits[a * L.WPD + ((uint32_t)j >> 5)], 1u << (j & 31));
+            }
         }
-        unsigned m = __ballot_sync(kFull, j >= 0);
-        if (j >= 0) {
-            ladj[run + __popc(m & ((1u << lane) - 1u))] = (uint16_t)j;
-            atomicAdd(&lofs[a], 1u);
-        }
-        run += __popc(m);
         a0 = __shfl_sync(kFull, a, 31);
     }
     __syncwarp();
-    // row counts -> offsets (exclusive scan over d + 1 entries)
+    // lengths -> padded offsets -> lists in ascending order
     running = 0;
     for (uint32_t c0 = 0; c0 <= d; c0 += 32) {
-        uint32_t i = c0 + lane;
-        uint32_t x = i <= d ? lofs[i] : 0;
+        uint32_t i = c0 + lane, x = 0;
+        if (i < d) {
+            uint32_t c = 0;
+            for (uint32_t t = 0; t < L.WPD; t++) c += __popc(bits[i * L.WPD + t]);
+            len[i] = (uint16_t)c;
+            x = round4(c);
+        }
         uint32_t incl = x;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             uint32_t y = __shfl_up_sync(kFull, incl, o);
             if (lane >= (unsigned)o) incl += y;
         }
-        __syncwarp();
         if (i <= d) lofs[i] = running + incl - x;
         running += __shfl_sync(kFull, incl, 31);
     }
     __syncwarp();
+    for (uint32_t i = lane; i < d; i += 32) {
+        uint32_t o = lofs[i];
+        for (uint32_t t = 0; t < L.WPD; t++) {
+            uint32_t m = bits[i * L.WPD + t];
+            while (m) {
+                ladj[o++] = (uint16_t)(t * 32 + (__ffs(m) - 1));
+                m &= m - 1;
+            }
+        }
+        while (o < lofs[i + 1]) ladj[o++] = kPad;
+    }
+    __syncwarp();
 
-    const LView v{nbr, lofs, ladj, d, u, k};
+    const LView v{nbr, lofs, len, ladj, d, u, k};
     if (k == 3) {
         // C = all of N+_u: every edge of the reduced DAG closes a triangle
         if (!LIST) {
-            if (lane == 0) cnt += lofs[d];
+            uint32_t c = 0;
+            for (uint32_t i = lane; i < d; i += 32) c += len[i];
+            cnt += c;
             return;
         }
-        for (uint32_t i = lane; i < d; i += 32) st.clist[i] = (uint16_t)i;
+        for (uint32_t i = lane; i < round4(d); i += 32) st.clist[i] = i < d ? (uint16_t)i : kPad;
         __syncwarp();
         lleaf<LIST>(v, st.clist, d, 0, d, 0, st, em, res, cnt, cks);
         return;
@@ -564,7 +610,7 @@ __device__ void sdegree_root_local(uint32_t u, uint32_t k, uint32_t D, const uin
 // stacks follow it in shared memory (lists move to the global arena when
 // they do not leave room for enough warps).
 struct CLay {
-    uint32_t D, WPD, NBR, RS, PRE, LOFS, HK, HV, P0, META, total;
+    uint32_t D, WPD, NBR, RS, PRE, LOFS, HK, HV, LEN, P0, META, total;
 };
 
 __host__ __device__ inline CLay make_clayout(uint32_t D) {
@@ -578,16 +624,19 @@ __host__ __device__ inline CLay make_clayout(uint32_t D) {
     L.LOFS = L.PRE + D + 1;    // D + 1
     L.HK = L.LOFS + D + 1;     // 2D
     L.HV = L.HK + 2 * D;       // 2D u16
-    L.P0 = L.HV + D;           // D u16: first-level children
+    L.LEN = L.HV + D;          // D u16: list lengths
+    L.P0 = L.LEN + D / 2;      // D u16: first-level children
     L.META = L.P0 + D / 2;     // 16 words
     L.total = (L.META + 16 + 3) & ~3u;
     return L;
 }
 
-// arena slice per CTA: directed bit-rows (D x WPD words) + reduced lists
+// arena slice per CTA: directed bit-rows (D x WPD words) + padded lists
 __host__ __device__ inline size_t cta_arena_words(uint32_t D) {
     CLay L = make_clayout(D);
-    return (size_t)D * L.WPD + ((size_t)D * (D - 1) / 2 + 1) / 2 + 4;
+    size_t rows = ((size_t)D * L.WPD + 3) & ~(size_t)3;
+    size_t lists = ((size_t)D * (D - 1) / 2 + 3 * (size_t)D + 1) / 2;
+    return (rows + lists + 3) & ~(size_t)3;
 }
 
 template <bool LIST>
@@ -607,11 +656,12 @@ __global__ void __launch_bounds__(512) k_sdegree_cta(uint32_t k, uint32_t D, con
     uint32_t *lofs = smem + L.LOFS;
     uint32_t *hk = smem + L.HK;
     uint16_t *hv = reinterpret_cast<uint16_t *>(smem + L.HV);
+    uint16_t *len = reinterpret_cast<uint16_t *>(smem + L.LEN);
     uint16_t *p0 = reinterpret_cast<uint16_t *>(smem + L.P0);
     uint32_t *meta = smem + L.META;
     uint32_t *slice = arena + (size_t)blockIdx.x * cta_arena_words(D);
     uint32_t *bits = slice;
-    uint16_t *ladj_g = reinterpret_cast<uint16_t *>(slice + (size_t)D * L.WPD);
+    uint16_t *ladj_g = reinterpret_cast<uint16_t *>(slice + (((size_t)D * L.WPD + 3) & ~(size_t)3));
     unsigned long long cnt = 0, cks = 0;
     for (;;) {
         if (tid == 0) meta[15] = atomicAdd(queue, 1u);
@@ -681,11 +731,11 @@ __global__ void __launch_bounds__(512) k_sdegree_cta(uint32_t k, uint32_t D, con
             }
         }
         __syncthreads();
-        // ---- row lengths, longest row, offsets
+        // ---- row lengths, longest row, padded offsets
         for (uint32_t i = tid; i < d; i += nth) {
             uint32_t c = 0;
             for (uint32_t t = 0; t < L.WPD; t++) c += __popc(bits[i * L.WPD + t]);
-            lofs[i] = c;
+            len[i] = (uint16_t)c;
             atomicMax(&meta[3], c);
         }
         __syncthreads();
@@ -693,7 +743,7 @@ __global__ void __launch_bounds__(512) k_sdegree_cta(uint32_t k, uint32_t D, con
             uint32_t running = 0;
             for (uint32_t c0 = 0; c0 <= d; c0 += 32) {
                 uint32_t i = c0 + lane;
-                uint32_t x = i < d ? lofs[i] : 0;
+                uint32_t x = i < d ? round4(len[i]) : 0;
                 uint32_t incl = x;
 #pragma unroll
                 for (int o = 1; o < 32; o <<= 1) {
@@ -709,8 +759,7 @@ __global__ void __launch_bounds__(512) k_sdegree_cta(uint32_t k, uint32_t D, con
                 uint32_t cap = meta[3] ? meta[3] : 1;
                 uint32_t sw = stack_words(cap, k);
                 uint32_t budget = smem_words - L.total;
-                uint32_t lw = (lofs[d] + 1) / 2;
-                lw = (lw + 3) & ~3u;
+                uint32_t lw = (lofs[d] / 2 + 3) & ~3u;
                 uint32_t nw_g = budget / sw;
                 if (nw_g > nwarps) nw_g = nwarps;
                 uint32_t nw_s = lw <= budget ? (budget - lw) / sw : 0;
@@ -725,7 +774,7 @@ __global__ void __launch_bounds__(512) k_sdegree_cta(uint32_t k, uint32_t D, con
         }
         __syncthreads();
         uint16_t *ladj = meta[4] ? reinterpret_cast<uint16_t *>(smem + L.total) : ladj_g;
-        // ---- extraction: row i's bits in ascending order -> L(i)
+        // ---- extraction: row i's bits in ascending order -> L(i), padded
         for (uint32_t i = tid; i < d; i += nth) {
             uint32_t o = lofs[i];
             for (uint32_t t = 0; t < L.WPD; t++) {
@@ -735,10 +784,11 @@ __global__ void __launch_bounds__(512) k_sdegree_cta(uint32_t k, uint32_t D, con
                     m &= m - 1;
                 }
             }
+            while (o < lofs[i + 1]) ladj[o++] = kPad;
         }
         const uint32_t nw_dfs = meta[5], sw = meta[6];
         if (nw_dfs == 0 && tid == 0) atomicOr(&res->status, DEV_ERR_INTERNAL);  // no stack fits
-        const LView v{nbr, lofs, ladj, d, u, k};
+        const LView v{nbr, lofs, len, ladj, d, u, k};
         const uint32_t cap = meta[3] ? meta[3] : 1;
         // ---- first-level children (|L(w)| >= k-2), longest lists first
         if (k > 3 && warp == 0) {
@@ -751,7 +801,7 @@ __global__ void __launch_bounds__(512) k_sdegree_cta(uint32_t k, uint32_t D, con
                     uint32_t w = s + lane;
                     bool ok = false;
                     if (w < d) {
-                        uint32_t dw = lofs[w + 1] - lofs[w];
+                        uint32_t dw = len[w];
                         ok = dw + 2 >= k && dw >= lo && dw < hi;
                     }
                     unsigned m = __ballot_sync(kFull, ok);
@@ -762,14 +812,16 @@ __global__ void __launch_bounds__(512) k_sdegree_cta(uint32_t k, uint32_t D, con
             if (lane == 0) { meta[8] = n0; meta[9] = 0; }
         }
         if (k == 3 && LIST) {
-            for (uint32_t i = tid; i < d; i += nth) p0[i] = (uint16_t)i;
+            for (uint32_t i = tid; i < round4(d); i += nth) p0[i] = i < d ? (uint16_t)i : kPad;
         }
         __syncthreads();
         if (warp < nw_dfs) {
             const LStack st = stack_ptrs(smem + L.total + meta[7] + warp * sw, cap < d ? cap : d, k);
             if (k == 3) {
                 if (!LIST) {
-                    if (tid == 0) cnt += lofs[d];
+                    uint32_t c = 0;
+                    for (uint32_t i = tid; i < d; i += nw_dfs * 32) c += len[i];
+                    cnt += c;
                 } else {
                     // identity candidate list, split across the DFS warps
                     uint32_t chunk = (d + nw_dfs - 1) / nw_dfs;
