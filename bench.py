@@ -298,6 +298,165 @@ def run_reference(args, rank, world):
                     "d2h_bytes_per_step": 0}}
 
 
+# ------------------------------------------------------- batched form
+def run_batch(args):
+    """The batched workload: graph i = kclgen.batch_graph(i) (n log-uniform in
+    [50, 20000], mean degree 4-40, exponent 2.3, 0-5 planted cliques of size
+    8-16, k uniform in 3..9), count + checksum per graph, both orderings.
+    Compares one kcl_count_batch call with one library call per graph on the
+    same resident graphs; results must be identical."""
+    import torch
+
+    import kclgen
+    import paper_2203_13512_gb300 as kcl
+    G = args.batch_graphs
+    t0 = time.perf_counter()
+    data = [kclgen.batch_graph(i) for i in range(G)]
+    gen_s = time.perf_counter() - t0
+    graphs = [kcl.kcl_load_csr(rp, col) for rp, col, _ in data]
+    ks = [k for _, _, k in data]
+    b = kcl.kcl_batch_create()
+    out = {"metric": "graphs/s, batched vs one call per graph (count + checksum)",
+           "unit": "graphs/s", "higher_is_better": True, "n_gpus": 1,
+           "config": {"workload": "chung-lu-batch", "graphs": G,
+                      "vertices": int(sum(len(rp) - 1 for rp, _, _ in data)),
+                      "undirected_edges": int(sum(len(c) // 2 for _, c, _ in data)),
+                      "generation_s": round(gen_s, 1)},
+           "data": "synthetic (seeded Chung-Lu generator)", "orderings": {}}
+    total_per, total_bat, cliques = 0.0, 0.0, 0
+    for o in ("color", "degree"):
+        ords = [o] * G
+
+        def per_graph():
+            return [kcl.kcl_list(g, k, o, None)[:2] for g, k in zip(graphs, ks)]
+
+        def batched():
+            c, s = kcl.kcl_count_batch(b, graphs, ks, ords, checksums=True)
+            return list(zip(c, s))
+
+        ref = per_graph()  # warm-up (allocates each graph's scratch)
+        got = batched()
+        assert got == ref, "batched results differ from per-graph results"
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        per_graph()
+        torch.cuda.synchronize()
+        t_per = time.perf_counter() - t
+        t = time.perf_counter()
+        batched()
+        torch.cuda.synchronize()
+        t_bat = time.perf_counter() - t
+        n_cl = sum(c for c, _ in ref)
+        out["orderings"][o] = {"per_graph_s": round(t_per, 4), "batched_s": round(t_bat, 4),
+                               "per_graph_graphs_per_s": G / t_per, "batched_graphs_per_s": G / t_bat,
+                               "speedup": t_per / t_bat, "k_cliques": n_cl}
+        total_per += t_per
+        total_bat += t_bat
+        cliques += n_cl
+    out["value"] = 2 * G / total_bat
+    out["per_graph_value"] = 2 * G / total_per
+    out["speedup"] = total_per / total_bat
+    out["k_cliques_per_s_batched"] = cliques / total_bat
+    out["bit_exact"] = True
+    b.free()
+    return out
+
+
+# ------------------------------------------------------- served form
+def run_serve(args):
+    """The served workload: 64 resident graphs -- ids 1-32 R-MAT at scale
+    12 + (id mod 5), ids 33-64 graph `id` of the batched workload -- and a
+    Poisson stream of (graph, k in 3..8, count | count + checksum) queries
+    (seed 1).  The server (8 slots, 100 GB scratch budget, continuous
+    batching) is compared with a FIFO loop that runs one query at a time in
+    arrival order; every served result must equal the FIFO result."""
+    import numpy as np
+    import torch
+
+    import kclgen
+    import paper_2203_13512_gb300 as kcl
+    graphs = [kcl.kcl_load_csr(*kclgen.rmat20(seed=i, scale=12 + i % 5)) for i in range(1, 33)]
+    graphs += [kcl.kcl_load_csr(*kclgen.batch_graph(i)[:2]) for i in range(33, 65)]
+    rng = np.random.default_rng(1)
+    Q = args.serve_queries
+    qs = [(int(rng.integers(64)), int(rng.integers(3, 9)),
+           "color" if rng.random() < 0.5 else "degree", bool(rng.random() < 0.5)) for _ in range(Q)]
+    gaps = rng.exponential(1.0, Q)
+
+    def run_one(q):
+        gi, k, o, lst = q
+        if lst:
+            c, h, _, _ = kcl.kcl_list(graphs[gi], k, o, None)
+            return c, h
+        return kcl.kcl_count(graphs[gi], k, o), 0
+
+    # FIFO single-server loop: service time of each query measured once
+    for q in qs[:64]:
+        run_one(q)  # warm-up
+    service, ref = [], []
+    for q in qs:
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        ref.append(run_one(q))
+        service.append(time.perf_counter() - t)
+    out = {"metric": "served queries: throughput and latency, continuous batching vs FIFO",
+           "unit": "queries/s", "higher_is_better": True, "n_gpus": 1,
+           "config": {"workload": "served-mixed", "graphs": 64, "queries": Q,
+                      "rmat_scales": "12..16", "k": "3..8", "slots": 8,
+                      "scratch_budget_gb": 100},
+           "data": "synthetic", "rates": {}}
+    for rate in args.serve_rates:
+        arr = np.cumsum(gaps / rate)
+        done, lat = 0.0, []
+        for a, sv in zip(arr, service):
+            done = max(a, done) + sv
+            lat.append(done - a)
+        fifo = {"throughput_qps": Q / done, "p50_ms": 1e3 * float(np.percentile(lat, 50)),
+                "p99_ms": 1e3 * float(np.percentile(lat, 99))}
+        srv = kcl.kcl_server_create(slots=8, scratch_budget_bytes=100 << 30, small_nnz=1 << 20)
+        ids = [kcl.kcl_server_add_graph(srv, g) for g in graphs]
+        for gi in range(8):  # warm the slots' scratch on the larger graphs
+            kcl.kcl_server_wait(srv, kcl.kcl_server_submit(srv, ids[gi], 4, "color"))
+        base = kcl.kcl_server_clock(srv)
+        tickets = []
+        for (gi, k, o, lst), a in zip(qs, arr):
+            while kcl.kcl_server_clock(srv) - base < a:
+                time.sleep(0)
+            tickets.append(kcl.kcl_server_submit(srv, ids[gi], k, o, lst))
+        res = [kcl.kcl_server_wait(srv, t) for t in tickets]
+        srv.destroy()
+        for r, want, q in zip(res, ref, qs):
+            assert r["status"] == 0 and (r["count"], r["checksum"]) == want, q
+        slat = [r["done_s"] - r["submit_s"] for r in res]
+        makespan = max(r["done_s"] for r in res) - base
+        out["rates"][str(rate)] = {
+            "served": {"throughput_qps": Q / makespan,
+                       "p50_ms": 1e3 * float(np.percentile(slat, 50)),
+                       "p99_ms": 1e3 * float(np.percentile(slat, 99)),
+                       "mean_batch": float(np.mean([r["batch"] for r in res]))},
+            "fifo": fifo}
+    last = out["rates"][str(args.serve_rates[-1])]
+    out["value"] = last["served"]["throughput_qps"]
+    out["bit_exact"] = True
+    return out
+
+
+def profile_case(spec):
+    """A single library call on a smaller R-MAT graph (for ncu captures)."""
+    import kclgen
+    import paper_2203_13512_gb300 as kcl
+    parts = spec.split(":")
+    scale, k, ordering = int(parts[0]), int(parts[1]), parts[2]
+    mode = parts[3] if len(parts) > 3 else "count"
+    rp, col = kclgen.rmat20(seed=1, scale=scale)
+    g = kcl.kcl_load_csr(rp, col)
+    if mode == "count":
+        print(kcl.kcl_count(g, k, ordering))
+    else:
+        print(kcl.kcl_list(g, k, ordering, None))
+    g.free()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -305,7 +464,23 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--form", default="single", choices=["single", "batch", "serve"],
+                    help="single: the R-MAT scale-20 line; batch / serve: the batched and "
+                         "served workloads, each printing its own JSON line")
+    ap.add_argument("--batch-graphs", type=int, default=512)
+    ap.add_argument("--serve-queries", type=int, default=4000)
+    ap.add_argument("--serve-rates", type=float, nargs="+", default=[1000.0, 10000.0])
+    ap.add_argument("--profile-case", default=None,
+                    help="SCALE:K:ORDERING[:count|list] -- one call on R-MAT at SCALE "
+                         "(16 * 2^SCALE edges, seed 1), for profilers")
     args = ap.parse_args()
+    if args.profile_case:
+        profile_case(args.profile_case)
+        return
+    if args.form != "single":
+        res = run_batch(args) if args.form == "batch" else run_serve(args)
+        print(json.dumps(res))
+        return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if world > 1:

@@ -94,6 +94,12 @@ kcl_status kcl_load_csr(uint32_t n, const uint64_t *row_ptr, const uint32_t *col
 /* Release a graph and all device memory it owns.  NULL is ignored. */
 void kcl_free_graph(kcl_graph *g);
 
+/* A second handle on a loaded graph: it shares g's device CSR (g must
+ * outlive it) but has its own scratch and stream, so calls on the two
+ * handles may run concurrently.  Free it with kcl_free_graph (the CSR stays
+ * with g).  Library facility; the paper has none. */
+kcl_status kcl_graph_view(const kcl_graph *g, void *stream, kcl_graph **out);
+
 /* Change the stream that later calls on g are ordered on. */
 kcl_status kcl_set_stream(kcl_graph *g, void *stream);
 
@@ -134,6 +140,59 @@ kcl_status kcl_stage_info(kcl_graph *g, uint32_t k, kcl_ordering ord, uint8_t *a
                           uint8_t *alive_final, uint32_t *outdeg, uint32_t *key,
                           uint64_t *prelist_count, uint32_t *max_outdeg);
 
+/* Batched counting (the batched form of the workload; the paper has none).
+ * A kcl_batch owns device scratch that is reused across calls; create it on
+ * the device and stream the batch's graphs live on.
+ * kcl_count_batch: gs[i] (loaded graphs, same device), ks[i] in [3,
+ *   KCL_MAX_K], ords[i] per graph.  Graphs that share (k, ordering) are joined
+ *   as one disjoint union on the device and counted by a single pass of the
+ *   pipeline (Algorithms 3-6); each root's count is attributed to its vertex
+ *   and summed per graph.  counts: host uint64[G], receives each graph's exact
+ *   k-clique count.  checksums: host uint64[G] or NULL; when given, each
+ *   graph's listing checksum (as kcl_list) is computed too.
+ * Errors: KCL_EINVAL, KCL_ENOMEM, KCL_ECUDA, KCL_ELIMIT (union beyond 2^32
+ *   vertices or edges, or a root above the out-degree limit). */
+typedef struct kcl_batch kcl_batch;
+kcl_status kcl_batch_create(void *stream, kcl_batch **out);
+void kcl_batch_free(kcl_batch *b);
+kcl_status kcl_count_batch(kcl_batch *b, kcl_graph *const *gs, const uint32_t *ks,
+                           const kcl_ordering *ords, uint32_t G, uint64_t *counts,
+                           uint64_t *checksums);
+
+/* Serving loop (a library facility; the paper has none).  Graphs stay
+ * resident (the caller's loaded handles, which must outlive the server);
+ * `slots` worker threads each own a CUDA stream and scratch, so admitted
+ * queries run concurrently and their work overlaps on the device.  A query
+ * is admitted while its scratch estimate fits in scratch_budget_bytes (a
+ * query larger than the whole budget runs alone).  Continuous batching: a
+ * free worker takes the oldest query; queries on graphs with at most
+ * small_nnz CSR entries are gathered with the other queued small-graph
+ * queries into one batched pass (as kcl_count_batch), and queued copies of
+ * the query it takes share its result.  Results are exact: equal to the same
+ * query run alone with kcl_count / kcl_list.
+ * Times in kcl_server_result are seconds on kcl_server_clock's steady clock
+ * (submission, start of the pass that answered it, completion); `batch` is
+ * the number of queries that pass answered. */
+typedef struct kcl_server kcl_server;
+typedef struct {
+    uint64_t count;
+    uint64_t checksum;   /* list = 1 queries; 0 otherwise */
+    double submit_s, start_s, done_s;
+    uint32_t batch;
+    kcl_status status;
+} kcl_server_result;
+kcl_status kcl_server_create(uint32_t slots, uint64_t scratch_budget_bytes, uint64_t small_nnz,
+                             kcl_server **out);
+kcl_status kcl_server_add_graph(kcl_server *s, kcl_graph *g, uint32_t *id);
+/* list = 0: count only; list = 1: count + checksum (no ring output). */
+kcl_status kcl_server_submit(kcl_server *s, uint32_t graph, uint32_t k, kcl_ordering ord, int list,
+                             uint64_t *ticket);
+kcl_status kcl_server_poll(kcl_server *s, uint64_t ticket, int *done, kcl_server_result *out);
+kcl_status kcl_server_wait(kcl_server *s, uint64_t ticket, kcl_server_result *out);
+double kcl_server_clock(const kcl_server *s);
+/* Finishes queued work, stops the workers and frees the server's scratch. */
+void kcl_server_destroy(kcl_server *s);
+
 /* Device time of the stages of the last kcl_count / kcl_list call on g, in
  * milliseconds, measured with CUDA events on the graph's stream when timing
  * is enabled (kcl_enable_timing).  stage ids: 0 Pre-Core, 1 Pre-List,
@@ -146,6 +205,10 @@ typedef struct {
 } kcl_timing;
 kcl_status kcl_enable_timing(kcl_graph *g, int enable);
 kcl_status kcl_last_timing(const kcl_graph *g, kcl_timing *t);
+/* The same for a batch: stage times summed over the (k, ordering) groups of
+ * the last kcl_count_batch call; *groups receives the number of groups. */
+kcl_status kcl_batch_enable_timing(kcl_batch *b, int enable);
+kcl_status kcl_batch_last_timing(const kcl_batch *b, kcl_timing *t, uint32_t *groups);
 
 /* Allocation-free degeneracy ordering (the paper has no counterpart; this is
  * a library facility).  Some callers must not allocate device memory from

@@ -275,3 +275,187 @@ def kcl_degeneracy_order_noalloc(row_ptr, col, alive, degree, round_out, stream=
         _dev_ptr(degree, "int32", n), _dev_ptr(round_out, "int32", n),
         stream if stream is not None else _current_stream())
     _check(st, "kcl_degeneracy_order_noalloc")
+
+
+_lib.kcl_batch_create.argtypes = [_P, ctypes.POINTER(_P)]
+_lib.kcl_batch_create.restype = _I
+_lib.kcl_batch_free.argtypes = [_P]
+_lib.kcl_batch_free.restype = None
+_lib.kcl_count_batch.argtypes = [_P, _P, _P, _P, _U32, _P, _P]
+_lib.kcl_count_batch.restype = _I
+
+
+class Batch:
+    """Owning handle of a kcl_batch (device scratch reused across calls)."""
+
+    def __init__(self, handle):
+        self._h = handle
+
+    @property
+    def handle(self):
+        if self._h is None:
+            raise ValueError("batch already freed")
+        return self._h
+
+    def free(self):
+        if self._h is not None:
+            _lib.kcl_batch_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def kcl_batch_create(stream=None):
+    h = ctypes.c_void_p()
+    _check(_lib.kcl_batch_create(stream if stream is not None else _current_stream(),
+                                 ctypes.byref(h)), "kcl_batch_create")
+    return Batch(h)
+
+
+def kcl_batch_free(b):
+    b.free()
+
+
+def kcl_count_batch(b, graphs, ks, orderings, checksums=False):
+    """Counts (and optionally listing checksums) of many loaded graphs at
+    once: returns (counts, checksums-or-None) as lists."""
+    G = len(graphs)
+    handles = (ctypes.c_void_p * max(G, 1))(*[g.handle for g in graphs])
+    karr = np.ascontiguousarray(ks, dtype=np.uint32)
+    oarr = np.ascontiguousarray([_ord(o) for o in orderings], dtype=np.int32)
+    counts = np.zeros(max(G, 1), dtype=np.uint64)
+    cks = np.zeros(max(G, 1), dtype=np.uint64) if checksums else None
+    _check(_lib.kcl_count_batch(b.handle, ctypes.cast(handles, ctypes.c_void_p),
+                                karr.ctypes.data if G else None, oarr.ctypes.data if G else None,
+                                G, counts.ctypes.data, cks.ctypes.data if checksums else None),
+           "kcl_count_batch")
+    return ([int(x) for x in counts[:G]],
+            [int(x) for x in cks[:G]] if checksums else None)
+
+
+# ------------------------------------------------------------ views, server
+_lib.kcl_graph_view.argtypes = [_P, _P, ctypes.POINTER(_P)]
+_lib.kcl_graph_view.restype = _I
+
+
+def kcl_graph_view(g, stream=None):
+    """Second handle on a loaded graph (shared CSR, own scratch and stream)."""
+    h = ctypes.c_void_p()
+    _check(_lib.kcl_graph_view(g.handle, stream if stream is not None else _current_stream(),
+                               ctypes.byref(h)), "kcl_graph_view")
+    v = Graph(h, g.n, g.m)
+    v._parent = g  # the CSR belongs to g: keep it alive
+    return v
+
+
+class _ServerResult(ctypes.Structure):
+    _fields_ = [("count", ctypes.c_uint64), ("checksum", ctypes.c_uint64),
+                ("submit_s", ctypes.c_double), ("start_s", ctypes.c_double),
+                ("done_s", ctypes.c_double), ("batch", ctypes.c_uint32), ("status", ctypes.c_int)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+_lib.kcl_server_create.argtypes = [_U32, _U64, _U64, ctypes.POINTER(_P)]
+_lib.kcl_server_create.restype = _I
+_lib.kcl_server_add_graph.argtypes = [_P, _P, ctypes.POINTER(_U32)]
+_lib.kcl_server_add_graph.restype = _I
+_lib.kcl_server_submit.argtypes = [_P, _U32, _U32, _I, _I, ctypes.POINTER(_U64)]
+_lib.kcl_server_submit.restype = _I
+_lib.kcl_server_poll.argtypes = [_P, _U64, ctypes.POINTER(_I), ctypes.POINTER(_ServerResult)]
+_lib.kcl_server_poll.restype = _I
+_lib.kcl_server_wait.argtypes = [_P, _U64, ctypes.POINTER(_ServerResult)]
+_lib.kcl_server_wait.restype = _I
+_lib.kcl_server_clock.argtypes = [_P]
+_lib.kcl_server_clock.restype = ctypes.c_double
+_lib.kcl_server_destroy.argtypes = [_P]
+_lib.kcl_server_destroy.restype = None
+
+
+class Server:
+    """Handle of a kcl_server (see kcl_server_create)."""
+
+    def __init__(self, handle):
+        self._h = handle
+        self._graphs = []
+
+    @property
+    def handle(self):
+        if self._h is None:
+            raise ValueError("server already destroyed")
+        return self._h
+
+    def destroy(self):
+        if self._h is not None:
+            _lib.kcl_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+def kcl_server_create(slots=4, scratch_budget_bytes=100 << 30, small_nnz=1 << 20):
+    h = ctypes.c_void_p()
+    _check(_lib.kcl_server_create(slots, scratch_budget_bytes, small_nnz, ctypes.byref(h)),
+           "kcl_server_create")
+    return Server(h)
+
+
+def kcl_server_add_graph(s, g):
+    i = ctypes.c_uint32()
+    _check(_lib.kcl_server_add_graph(s.handle, g.handle, ctypes.byref(i)), "kcl_server_add_graph")
+    s._graphs.append(g)
+    return int(i.value)
+
+
+def kcl_server_submit(s, graph_id, k, ordering="color", listing=False):
+    t = ctypes.c_uint64()
+    _check(_lib.kcl_server_submit(s.handle, graph_id, k, _ord(ordering), 1 if listing else 0,
+                                  ctypes.byref(t)), "kcl_server_submit")
+    return int(t.value)
+
+
+def kcl_server_poll(s, ticket):
+    d, r = ctypes.c_int(), _ServerResult()
+    _check(_lib.kcl_server_poll(s.handle, ticket, ctypes.byref(d), ctypes.byref(r)), "kcl_server_poll")
+    return r.as_dict() if d.value else None
+
+
+def kcl_server_wait(s, ticket):
+    r = _ServerResult()
+    _check(_lib.kcl_server_wait(s.handle, ticket, ctypes.byref(r)), "kcl_server_wait")
+    return r.as_dict()
+
+
+def kcl_server_clock(s):
+    return float(_lib.kcl_server_clock(s.handle))
+
+
+def kcl_server_destroy(s):
+    s.destroy()
+
+
+_lib.kcl_batch_enable_timing.argtypes = [_P, _I]
+_lib.kcl_batch_enable_timing.restype = _I
+_lib.kcl_batch_last_timing.argtypes = [_P, ctypes.POINTER(_Timing), ctypes.POINTER(_U32)]
+_lib.kcl_batch_last_timing.restype = _I
+
+
+def kcl_batch_enable_timing(b, enable=True):
+    _check(_lib.kcl_batch_enable_timing(b.handle, 1 if enable else 0), "kcl_batch_enable_timing")
+
+
+def kcl_batch_last_timing(b):
+    t, gr = _Timing(), ctypes.c_uint32()
+    _check(_lib.kcl_batch_last_timing(b.handle, ctypes.byref(t), ctypes.byref(gr)),
+           "kcl_batch_last_timing")
+    return ({STAGES[i]: float(t.ms[i]) for i in range(KCL_NUM_STAGES)},
+            {STAGES[i]: int(t.launches[i]) for i in range(KCL_NUM_STAGES)}, int(gr.value))

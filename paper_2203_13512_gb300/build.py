@@ -17,7 +17,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(ROOT, "_build", "kcl")
 LIB = os.path.join(HERE, "libkcl.so")
-SOURCES = ["kcl_api.cu", "kcl_prep.cu", "kcl_bitcol.cu", "kcl_sdegree.cu"]
+SOURCES = ["kcl_api.cu", "kcl_prep.cu", "kcl_bitcol.cu", "kcl_sdegree.cu", "kcl_server.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

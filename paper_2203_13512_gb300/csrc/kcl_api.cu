@@ -16,14 +16,12 @@
 #include <string.h>
 
 #include <algorithm>
+#include <map>
 #include <new>
+#include <utility>
+#include <vector>
 
 #include "kcl_internal.cuh"
-
-namespace kcl {
-size_t bitcol_arena_words(uint32_t k, int num_sms, uint32_t max_outdeg);
-size_t sdegree_arena_words(uint32_t k, int num_sms, uint32_t max_outdeg);
-}  // namespace kcl
 
 using namespace kcl;
 
@@ -70,12 +68,26 @@ void free_workspace(Workspace &w) {
     w = Workspace();
 }
 
+// Grow the workspace to at least g's size.  Capacities only grow (by at least
+// half again), so handles that move between graphs of different sizes (batch
+// unions, server slots) settle instead of reallocating on every call.
 kcl_status ensure_workspace(kcl_graph *g) {
     Workspace &w = g->ws;
     if (w.res && w.n_cap >= g->n && w.nnz_cap >= g->nnz) return KCL_OK;
+    uint32_t n_new = g->n;
+    uint64_t nnz_new = g->nnz;
+    if (w.res) {
+        n_new = (uint32_t)std::min<uint64_t>(0xFFFFFFF0ull, std::max<uint64_t>(g->n, w.n_cap + w.n_cap / 2));
+        nnz_new = std::max<uint64_t>(g->nnz, w.nnz_cap + w.nnz_cap / 2);
+    }
+    size_t arena_words = w.arena_words;
+    uint32_t *arena = w.arena;
+    w.arena = nullptr;
     free_workspace(w);
-    size_t n = (size_t)g->n + 1;
-    size_t half = g->nnz / 2 + 1;
+    w.arena = arena;  // the arena is sized separately (ensure_arena)
+    w.arena_words = arena_words;
+    size_t n = (size_t)n_new + 1;
+    size_t half = nnz_new / 2 + 1;
     KCL_TRY(dev_alloc(&w.alive, n));
     KCL_TRY(dev_alloc(&w.alive_core, n));
     KCL_TRY(dev_alloc(&w.cdeg, n));
@@ -104,8 +116,8 @@ kcl_status ensure_workspace(kcl_graph *g) {
         return KCL_ENOMEM;
     }
     KCL_CK(cudaMemset(w.outdeg, 0, (n + 1) * sizeof(uint32_t)));
-    w.n_cap = g->n;
-    w.nnz_cap = g->nnz;
+    w.n_cap = n_new;
+    w.nnz_cap = nnz_new;
     return KCL_OK;
 }
 
@@ -305,7 +317,8 @@ kcl_status check_args(kcl_graph *g, uint32_t k, kcl_ordering ord) {
 
 // Full call: stages 0-3, results left in the pinned mirror.
 kcl_status run_call(kcl_graph *g, uint32_t k, kcl_ordering ord, const kcl_ring *ring, bool listing,
-                    unsigned long long *per_root) {
+                    unsigned long long *per_root, unsigned long long *per_root_cks = nullptr,
+                    const uint32_t *idmap = nullptr) {
     KCL_TRY(check_args(g, k, ord));
     if (cudaSetDevice(g->device) != cudaSuccess) return KCL_ECUDA;
     StageTimer T(g);
@@ -316,6 +329,8 @@ kcl_status run_call(kcl_graph *g, uint32_t k, kcl_ordering ord, const kcl_ring *
     ListArgs la;
     la.listing = listing ? 1 : 0;
     la.per_root = per_root;
+    la.per_root_cks = listing ? per_root_cks : nullptr;
+    la.idmap = idmap;
     if (listing && ring) {
         la.ring = ring->capacity ? ring->ids : nullptr;
         la.capacity = ring->capacity;
@@ -345,6 +360,110 @@ kcl_status total_count(const DevResult *r, uint64_t *count) {
     unsigned long long c = r->count + r->pre_count;
     if (r->count_carry || c < r->count) return KCL_EOVERFLOW;
     *count = c;
+    return KCL_OK;
+}
+
+}  // namespace
+
+// Batched form: graphs that share (k, ordering) are joined as a disjoint
+// union on the device and counted in one pipeline pass; each root's (and
+// each Pre-List component's) count and checksum are attributed to its
+// vertex, and a per-graph reduction gives every graph's own result.
+struct kcl_batch {
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    kcl_graph *ug = nullptr;  // the union graph (CSR and workspace reused)
+    uint32_t n_cap = 0;
+    uint64_t nnz_cap = 0;
+    uint32_t *graph_of = nullptr, *idmap = nullptr;
+    unsigned long long *vcount = nullptr, *vcks = nullptr;
+    unsigned long long *gcount = nullptr, *gcks = nullptr;
+    BatchSrc *d_src = nullptr;
+    uint32_t g_cap = 0;
+    std::vector<BatchSrc> h_src;
+    std::vector<unsigned long long> h_count, h_cks;
+    kcl_timing timing = {};  // stage times summed over the groups of the last call
+    uint32_t groups = 0;
+};
+
+namespace {
+
+kcl_status batch_reserve(kcl_batch *b, uint32_t n, uint64_t nnz, uint32_t G) {
+    kcl_graph *ug = b->ug;
+    if (n > b->n_cap || nnz > b->nnz_cap) {
+        uint32_t nc = std::max(n, b->n_cap);
+        uint64_t ec = std::max(nnz, b->nnz_cap);
+        KCL_TRY(dev_alloc(&ug->rp, (size_t)nc + 1));
+        KCL_TRY(dev_alloc(&ug->col, ec ? ec : 1));
+        KCL_TRY(dev_alloc(&b->graph_of, (size_t)nc + 1));
+        KCL_TRY(dev_alloc(&b->idmap, (size_t)nc + 1));
+        KCL_TRY(dev_alloc(&b->vcount, (size_t)nc + 1));
+        KCL_TRY(dev_alloc(&b->vcks, (size_t)nc + 1));
+        b->n_cap = nc;
+        b->nnz_cap = ec;
+    }
+    if (G > b->g_cap) {
+        KCL_TRY(dev_alloc(&b->d_src, G));
+        KCL_TRY(dev_alloc(&b->gcount, G));
+        KCL_TRY(dev_alloc(&b->gcks, G));
+        b->g_cap = G;
+    }
+    return KCL_OK;
+}
+
+// One (k, ordering) group of a batch.
+kcl_status batch_group(kcl_batch *b, kcl_graph *const *gs, const std::vector<uint32_t> &idx, uint32_t k,
+                       kcl_ordering ord, bool listing, uint64_t *counts, uint64_t *checksums) {
+    const uint32_t G = (uint32_t)idx.size();
+    b->h_src.resize(G);
+    uint64_t voff = 0, eoff = 0;
+    for (uint32_t i = 0; i < G; i++) {
+        const kcl_graph *g = gs[idx[i]];
+        b->h_src[i] = BatchSrc{g->rp, g->col, g->n, (uint32_t)voff, g->nnz, eoff};
+        voff += g->n;
+        eoff += g->nnz;
+    }
+    if (voff > 0xFFFFFFF0ull || eoff / 2 > 0xFFFFFFF0ull) return KCL_ELIMIT;
+    const uint32_t n = (uint32_t)voff;
+    KCL_TRY(batch_reserve(b, n, eoff, G));
+    kcl_graph *ug = b->ug;
+    cudaStream_t s = b->stream;
+    KCL_CK(cudaMemcpyAsync(b->d_src, b->h_src.data(), G * sizeof(BatchSrc), cudaMemcpyHostToDevice, s));
+    launch_union_build(b->d_src, G, n, ug->rp, ug->col, b->graph_of, b->idmap, s);
+    ug->n = n;
+    ug->nnz = eoff;
+    ug->stream = s;
+    KCL_CK(cudaMemsetAsync(b->vcount, 0, ((size_t)n + 1) * sizeof(unsigned long long), s));
+    if (listing) KCL_CK(cudaMemsetAsync(b->vcks, 0, ((size_t)n + 1) * sizeof(unsigned long long), s));
+    KCL_TRY(ensure_workspace(ug));
+    ug->ws.vcount_pre = b->vcount;
+    ug->ws.vcks_pre = listing ? b->vcks : nullptr;
+    ug->ws.idmap = b->idmap;
+    kcl_status st = n ? run_call(ug, k, ord, nullptr, listing, b->vcount, b->vcks, b->idmap) : KCL_OK;
+    ug->ws.vcount_pre = nullptr;
+    ug->ws.vcks_pre = nullptr;
+    ug->ws.idmap = nullptr;
+    if (st != KCL_OK) return st;
+    if (ug->timing.enabled && n)
+        for (int i = 0; i < KCL_NUM_STAGES; i++) {
+            b->timing.ms[i] += ug->timing.ms[i];
+            b->timing.launches[i] += ug->timing.launches[i];
+        }
+    b->groups++;
+    launch_graph_sums(b->d_src, G, b->vcount, listing ? b->vcks : nullptr, b->gcount,
+                      listing ? b->gcks : nullptr, s);
+    b->h_count.resize(G);
+    b->h_cks.resize(G);
+    KCL_CK(cudaMemcpyAsync(b->h_count.data(), b->gcount, G * sizeof(unsigned long long),
+                           cudaMemcpyDeviceToHost, s));
+    if (listing)
+        KCL_CK(cudaMemcpyAsync(b->h_cks.data(), b->gcks, G * sizeof(unsigned long long),
+                               cudaMemcpyDeviceToHost, s));
+    KCL_CK(cudaStreamSynchronize(s));
+    for (uint32_t i = 0; i < G; i++) {
+        counts[idx[i]] = b->h_count[i];
+        if (listing) checksums[idx[i]] = b->h_cks[i];
+    }
     return KCL_OK;
 }
 
@@ -422,12 +541,30 @@ void kcl_free_graph(kcl_graph *g) {
     else cudaDeviceSynchronize();
     (void)cudaGetLastError();
     free_workspace(g->ws);
-    if (g->rp) cudaFree(g->rp);
-    if (g->col) cudaFree(g->col);
+    if (g->owns_csr && g->rp) cudaFree(g->rp);
+    if (g->owns_csr && g->col) cudaFree(g->col);
     for (int i = 0; i < 2 * KCL_NUM_STAGES; i++)
         if (g->timing.ev[i]) cudaEventDestroy(g->timing.ev[i]);
     (void)cudaGetLastError();
     delete g;
+}
+
+kcl_status kcl_graph_view(const kcl_graph *g, void *stream, kcl_graph **out) {
+    if (!g || !out) return KCL_EINVAL;
+    *out = nullptr;
+    kcl_graph *v = new (std::nothrow) kcl_graph();
+    if (!v) return KCL_ENOMEM;
+    v->n = g->n;
+    v->nnz = g->nnz;
+    v->device = g->device;
+    v->num_sms = g->num_sms;
+    v->stream = (cudaStream_t)stream;
+    v->rp = g->rp;
+    v->col = g->col;
+    v->max_deg = g->max_deg;
+    v->owns_csr = false;
+    *out = v;
+    return KCL_OK;
 }
 
 kcl_status kcl_set_stream(kcl_graph *g, void *stream) {
@@ -490,6 +627,68 @@ kcl_status kcl_stage_info(kcl_graph *g, uint32_t k, kcl_ordering ord, uint8_t *a
     KCL_CK(cudaStreamSynchronize(g->stream));
     if (prelist_count) *prelist_count = fe.pre_count;
     if (max_outdeg) *max_outdeg = fe.max_outdeg;
+    return KCL_OK;
+}
+
+kcl_status kcl_batch_create(void *stream, kcl_batch **out) {
+    if (!out) return KCL_EINVAL;
+    *out = nullptr;
+    kcl_batch *b = new (std::nothrow) kcl_batch();
+    if (!b) return KCL_ENOMEM;
+    b->stream = (cudaStream_t)stream;
+    b->ug = new (std::nothrow) kcl_graph();
+    if (!b->ug || cudaGetDevice(&b->device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&b->ug->num_sms, cudaDevAttrMultiProcessorCount, b->device) != cudaSuccess) {
+        (void)cudaGetLastError();
+        kcl_batch_free(b);
+        return KCL_ECUDA;
+    }
+    b->ug->device = b->device;
+    b->ug->stream = b->stream;
+    *out = b;
+    return KCL_OK;
+}
+
+void kcl_batch_free(kcl_batch *b) {
+    if (!b) return;
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    else cudaDeviceSynchronize();
+    (void)cudaGetLastError();
+    void *ptrs[] = {b->graph_of, b->idmap, b->vcount, b->vcks, b->gcount, b->gcks, b->d_src};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    kcl_free_graph(b->ug);
+    delete b;
+}
+
+kcl_status kcl_count_batch(kcl_batch *b, kcl_graph *const *gs, const uint32_t *ks,
+                           const kcl_ordering *ords, uint32_t G, uint64_t *counts,
+                           uint64_t *checksums) {
+    if (!b || (G && (!gs || !ks || !ords || !counts))) return KCL_EINVAL;
+    std::map<std::pair<uint32_t, int>, std::vector<uint32_t>> groups;
+    for (uint32_t i = 0; i < G; i++) {
+        if (!gs[i] || gs[i]->device != b->device) return KCL_EINVAL;
+        KCL_TRY(check_args(gs[i], ks[i], ords[i]));
+        groups[{ks[i], (int)ords[i]}].push_back(i);
+    }
+    if (cudaSetDevice(b->device) != cudaSuccess) return KCL_ECUDA;
+    b->timing = kcl_timing{};
+    b->groups = 0;
+    for (auto &kv : groups)
+        KCL_TRY(batch_group(b, gs, kv.second, kv.first.first, (kcl_ordering)kv.first.second,
+                            checksums != nullptr, counts, checksums));
+    return KCL_OK;
+}
+
+kcl_status kcl_batch_enable_timing(kcl_batch *b, int enable) {
+    if (!b) return KCL_EINVAL;
+    return kcl_enable_timing(b->ug, enable);
+}
+
+kcl_status kcl_batch_last_timing(const kcl_batch *b, kcl_timing *t, uint32_t *groups) {
+    if (!b || !t) return KCL_EINVAL;
+    *t = b->timing;
+    if (groups) *groups = b->groups;
     return KCL_OK;
 }
 

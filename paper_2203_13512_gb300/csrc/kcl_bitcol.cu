@@ -296,6 +296,8 @@ struct Emit {
     uint32_t *ring;
     unsigned long long capacity;
     int wrap;
+    unsigned long long *root_cks;  // listing: per-root checksum sums, or null
+    const uint32_t *idmap;         // listing: vertex -> output id, or null (identity)
 };
 
 struct View {  // read-only view of a built subproblem, per warp
@@ -538,8 +540,14 @@ __global__ void __launch_bounds__(128) k_bitcol_warp(uint32_t k, const uint32_t 
         const uint32_t u = roots[begin + idx];
         const uint32_t base = optr[u], d = optr[u + 1] - base;
         const unsigned long long before = cnt;
+        const unsigned long long before_cks = cks;
         build_sub<1, WT>(d, base, WT, optr, oadj, s);
-        View v{s.B, s.colp, s.start, s.ids, d, WT, L.WP, s.meta[0], u, k};
+        if (LIST && em.idmap) {  // output ids (batched unions map back to each graph's ids)
+            for (uint32_t i = lane; i < d; i += 32) s.ids[i] = em.idmap[s.ids[i]];
+            __syncwarp();
+        }
+        const uint32_t uo = (LIST && em.idmap) ? em.idmap[u] : u;
+        View v{s.B, s.colp, s.start, s.ids, d, WT, L.WP, s.meta[0], uo, k};
         if (k == 3) {
             const uint32_t dw = (d + 31) >> 5;
             for (uint32_t t = lane; t < WT; t += 32)
@@ -555,6 +563,11 @@ __global__ void __launch_bounds__(128) k_bitcol_warp(uint32_t k, const uint32_t 
             unsigned long long mine = cnt - before;
             for (int o = 16; o > 0; o >>= 1) mine += __shfl_down_sync(kFull, mine, o);
             if (lane == 0 && mine) atomicAdd(&per_root[u], mine);
+        }
+        if (LIST && em.root_cks) {
+            unsigned long long mine = cks - before_cks;
+            for (int o = 16; o > 0; o >>= 1) mine += __shfl_down_sync(kFull, mine, o);
+            if (lane == 0 && mine) atomicAdd(&em.root_cks[u], mine);
         }
         __syncwarp();
     }
@@ -600,8 +613,14 @@ __global__ void __launch_bounds__(NW * 32) k_bitcol_cta(uint32_t k, uint32_t W,
         const uint32_t u = roots[begin + idx];
         const uint32_t base = optr[u], d = optr[u + 1] - base;
         const unsigned long long before = cnt;
+        const unsigned long long before_cks = cks;
         build_sub<NW, 0>(d, base, W, optr, oadj, s);
-        View v{s.B, s.colp, s.start, s.ids, d, W, L.WP, s.meta[0], u, k};
+        if (LIST && em.idmap) {  // output ids (batched unions map back to each graph's ids)
+            for (uint32_t i = threadIdx.x; i < d; i += blockDim.x) s.ids[i] = em.idmap[s.ids[i]];
+            __syncthreads();
+        }
+        const uint32_t uo = (LIST && em.idmap) ? em.idmap[u] : u;
+        View v{s.B, s.colp, s.start, s.ids, d, W, L.WP, s.meta[0], uo, k};
         if (k == 3) {
             const uint32_t dw = (d + 31) >> 5;
             for (uint32_t t = lane; t < W; t += 32)
@@ -623,6 +642,11 @@ __global__ void __launch_bounds__(NW * 32) k_bitcol_cta(uint32_t k, uint32_t W,
             unsigned long long mine = cnt - before;
             for (int o = 16; o > 0; o >>= 1) mine += __shfl_down_sync(kFull, mine, o);
             if (lane == 0 && mine) atomicAdd(&per_root[u], mine);
+        }
+        if (LIST && em.root_cks) {
+            unsigned long long mine = cks - before_cks;
+            for (int o = 16; o > 0; o >>= 1) mine += __shfl_down_sync(kFull, mine, o);
+            if (lane == 0 && mine) atomicAdd(&em.root_cks[u], mine);
         }
         __syncthreads();
     }
@@ -681,7 +705,7 @@ void launch_warp(uint32_t k, Workspace &w, uint32_t begin, uint32_t end, unsigne
                  unsigned long long *per_root, int wpb, size_t smem, int num_sms, cudaStream_t s) {
     auto kern = k_bitcol_warp<WT, LIST>;
     int occ = 0;
-    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+    if (!allow_max_smem(kern) ||
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, wpb * 32, smem) != cudaSuccess)
         (void)cudaGetLastError();
     if (occ < 1) occ = 1;
@@ -697,7 +721,7 @@ void launch_cta(uint32_t k, uint32_t W, int nw, Workspace &w, uint32_t begin, ui
                 uint32_t blocks, int num_sms, cudaStream_t s) {
     auto kern = k_bitcol_cta<NW, LIST, AG, BG>;
     int occ = 0;
-    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+    if (!allow_max_smem(kern) ||
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, nw * 32, smem) != cudaSuccess)
         (void)cudaGetLastError();
     if (occ < 1) occ = 1;
@@ -730,7 +754,7 @@ size_t bitcol_arena_words(uint32_t k, int num_sms, uint32_t max_outdeg) {
 int launch_bitcol(const kcl_graph *g, uint32_t k, Workspace &w, const uint32_t *class_begin,
                   int n_classes, const ListArgs &la, cudaStream_t s) {
     // class c covers root positions [class_begin[c], c ? class_begin[c-1] : n_roots)
-    Emit em{la.ring, la.capacity, la.wrap};
+    Emit em{la.ring, la.capacity, la.wrap, la.per_root_cks, la.idmap};
     int launches = 0;
     cudaMemsetAsync(w.queue, 0, 64 * sizeof(unsigned), s);
     for (int c = 0; c < n_classes; c++) {
@@ -740,7 +764,16 @@ int launch_bitcol(const kcl_graph *g, uint32_t k, Workspace &w, const uint32_t *
         const ClassCfg &cc = kClass[c];
         unsigned *q = w.queue + c;
         const size_t smem = class_smem(c, k);
-        if (!cc.cta) {
+        if (!cc.cta && la.listing) {
+            // listing: every clique is hashed one by one, so a root's cost grows
+            // with its clique count; a CTA of 4 warps shares each root's
+            // first-level children (counting keeps one warp per root)
+            const size_t sm4 = ((size_t)sub_layout(cc.W, false, false).total + 4 * dfs_words(cc.W, k)) * 4;
+            uint32_t blocks = (uint32_t)g->num_sms * 8;
+            if (blocks > end - begin) blocks = end - begin;
+            launch_cta<4, true, false, false>(k, cc.W, 4, w, begin, end, q, em, la.per_root, sm4,
+                                              blocks, g->num_sms, s);
+        } else if (!cc.cta) {
 #define KCL_W(WV)                                                                              \
     if (la.listing) launch_warp<WV, true>(k, w, begin, end, q, em, la.per_root, cc.nw, smem, g->num_sms, s); \
     else launch_warp<WV, false>(k, w, begin, end, q, em, la.per_root, cc.nw, smem, g->num_sms, s);

@@ -46,6 +46,16 @@ struct PeelCtl {
     unsigned pad[6];
 };
 
+// One graph of a batch: its device CSR and its place in the disjoint union.
+struct BatchSrc {
+    const uint64_t *rp;
+    const uint32_t *col;
+    uint32_t n;
+    uint32_t voff;
+    uint64_t nnz;
+    uint64_t eoff;
+};
+
 // Workspace owned by a graph, grown on demand and reused across calls.
 struct Workspace {
     uint8_t *alive = nullptr;        // n
@@ -73,6 +83,9 @@ struct Workspace {
     DevResult *res = nullptr;
     DevResult *h_res = nullptr;      // pinned host mirror
     PeelCtl *peel = nullptr;         // single-launch peel control block
+    unsigned long long *vcount_pre = nullptr;  // batch: Pre-List counts by component root
+    unsigned long long *vcks_pre = nullptr;    // batch: Pre-List checksums by component root
+    const uint32_t *idmap = nullptr;           // batch: union vertex -> graph's own id
     uint32_t n_cap = 0;
     uint64_t nnz_cap = 0;
 };
@@ -95,6 +108,7 @@ struct kcl_graph {
     uint64_t *rp = nullptr;    // device CSR
     uint32_t *col = nullptr;
     uint32_t max_deg = 0;
+    bool owns_csr = true;      // false for a view that shares another graph's CSR
     kcl::Workspace ws;
     kcl::Timing timing;
 };
@@ -165,6 +179,45 @@ __device__ __forceinline__ void hash_size(uint32_t d, uint32_t *T, uint32_t *shi
     *shift = 32 - lg;
 }
 
+// Largest dynamic shared memory a block may opt in to on the current device.
+// Kernels get their MaxDynamicSharedMemorySize attribute set to this value
+// (never to a call-specific size): the attribute is per-function state, and
+// calls running concurrently on several host threads must not shrink it
+// under each other.
+inline int max_dynamic_smem() {
+    static int cached[64] = {0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        (void)cudaGetLastError();
+        dev = 0;
+    }
+    if (dev >= 0 && dev < 64 && cached[dev]) return cached[dev];
+    int v = 48 * 1024;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) {
+        (void)cudaGetLastError();
+        v = 48 * 1024;
+    }
+    if (dev >= 0 && dev < 64) cached[dev] = v;
+    return v;
+}
+
+// Let `kern` use as much dynamic shared memory as the device allows next to
+// its static shared memory.  Returns false if the attribute cannot be set.
+template <typename K>
+inline bool allow_max_smem(K kern) {
+    cudaFuncAttributes fa;
+    if (cudaFuncGetAttributes(&fa, kern) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return false;
+    }
+    int lim = max_dynamic_smem() - (int)fa.sharedSizeBytes;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, lim) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return false;
+    }
+    return true;
+}
+
 // ------------------------------------------------------ host-side launchers
 // Every launcher enqueues on `s` and returns the number of kernel launches.
 
@@ -192,6 +245,11 @@ int launch_roots(const kcl_graph *g, uint32_t k, Workspace &w, uint32_t max_outd
                  cudaStream_t s);
 int launch_exclusive_scan(const uint32_t *in, uint32_t *out, uint32_t n, uint32_t *block_tmp,
                           cudaStream_t s);
+int launch_union_build(const BatchSrc *src, uint32_t G, uint32_t n_total, uint64_t *urp,
+                       uint32_t *ucol, uint32_t *graph_of, uint32_t *idmap, cudaStream_t s);
+int launch_graph_sums(const BatchSrc *src, uint32_t G, const unsigned long long *vcount,
+                      const unsigned long long *vcks, unsigned long long *out_count,
+                      unsigned long long *out_cks, cudaStream_t s);
 
 // kcl_bitcol.cu
 struct ListArgs {
@@ -200,6 +258,8 @@ struct ListArgs {
     int wrap = 0;
     int listing = 0;
     unsigned long long *per_root = nullptr;
+    unsigned long long *per_root_cks = nullptr;  // listing: checksum per root
+    const uint32_t *idmap = nullptr;             // listing: vertex -> output id
 };
 int bitcol_classes(uint32_t *limits, int max);
 int launch_bitcol(const kcl_graph *g, uint32_t k, Workspace &w, const uint32_t *class_begin,
@@ -207,6 +267,8 @@ int launch_bitcol(const kcl_graph *g, uint32_t k, Workspace &w, const uint32_t *
 
 // kcl_sdegree.cu
 int sdegree_classes(uint32_t *limits, int max);
+size_t sdegree_arena_words(uint32_t k, int num_sms, uint32_t max_outdeg);
+size_t bitcol_arena_words(uint32_t k, int num_sms, uint32_t max_outdeg);
 int launch_sdegree(const kcl_graph *g, uint32_t k, Workspace &w, const uint32_t *class_begin,
                    int n_classes, const ListArgs &la, cudaStream_t s);
 

@@ -184,7 +184,7 @@ __device__ unsigned long long binom64(unsigned long long n, unsigned k, bool *ov
 __global__ void k_uf_check(uint32_t n, uint32_t k, const uint8_t *__restrict__ alive,
                            const uint32_t *__restrict__ parent, const uint32_t *__restrict__ comp_n,
                            const unsigned long long *__restrict__ comp_sdeg, uint32_t *comp_flag,
-                           uint32_t *comp_slot, DevResult *res) {
+                           uint32_t *comp_slot, unsigned long long *vcount, DevResult *res) {
     for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
         if (!alive[v] || parent[v] != v) continue;
         unsigned long long nc = comp_n[v];
@@ -193,6 +193,7 @@ __global__ void k_uf_check(uint32_t n, uint32_t k, const uint8_t *__restrict__ a
         unsigned long long c = binom64(nc, k, &ovf);
         if (ovf) atomicOr(&res->status, DEV_ERR_OVERFLOW);
         add_count(&res->pre_count, &res->count_carry, c);
+        if (vcount && c) atomicAdd(&vcount[v], c);  // attributed to the component's root
         uint32_t slot = atomicAdd(&res->n_clique_comps, 1u);
         comp_flag[v] = 1;
         if (comp_slot) comp_slot[v] = slot;
@@ -255,7 +256,9 @@ __device__ unsigned long long binom_small(unsigned long long n, unsigned k) {
 
 __global__ void k_comp_emit(uint32_t k, const uint32_t *__restrict__ offs,
                             const uint32_t *__restrict__ sizes, const uint32_t *__restrict__ members,
-                            uint32_t *ring, unsigned long long capacity, int wrap, DevResult *res) {
+                            uint32_t *ring, unsigned long long capacity, int wrap,
+                            const uint32_t *__restrict__ croots, unsigned long long *vcks,
+                            const uint32_t *__restrict__ idmap, DevResult *res) {
     uint32_t s = blockIdx.x;
     const uint32_t *m = members + offs[s];
     uint32_t nc = sizes[s];
@@ -277,7 +280,7 @@ __global__ void k_comp_emit(uint32_t k, const uint32_t *__restrict__ offs,
             }
             c = lo;
             rem -= binom_small(c, i);
-            ids[i - 1] = m[c];
+            ids[i - 1] = idmap ? idmap[m[c]] : m[c];
             hi = c;
         }
         uint64_t h = hash_seed(k);
@@ -291,6 +294,7 @@ __global__ void k_comp_emit(uint32_t k, const uint32_t *__restrict__ offs,
         }
     }
     atomicAdd(&res->pre_checksum, local_sum);
+    if (vcks && local_sum) atomicAdd(&vcks[croots[s]], local_sum);
 }
 
 // -------------------------------------------------------- orientations
@@ -630,6 +634,61 @@ __global__ void k_scan_add(uint32_t *out, uint32_t n, const uint32_t *__restrict
 }  // namespace
 
 // ====================================================== host launchers
+// ---------------------------------------------------------- batching
+// Disjoint union of a batch of graphs: block b copies graph b's rows and
+// columns with its vertex offset voff[b] and edge offset eoff[b].
+__global__ void k_union_build(const BatchSrc *__restrict__ src, uint32_t n_total, uint64_t *urp,
+                              uint32_t *ucol, uint32_t *graph_of, uint32_t *idmap) {
+    const BatchSrc b = src[blockIdx.x];
+    for (uint32_t v = threadIdx.x; v < b.n; v += blockDim.x) {
+        urp[b.voff + v] = b.rp[v] + b.eoff;
+        graph_of[b.voff + v] = blockIdx.x;
+        idmap[b.voff + v] = v;
+    }
+    for (uint64_t e = threadIdx.x; e < b.nnz; e += blockDim.x) ucol[b.eoff + e] = b.col[e] + b.voff;
+    if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) urp[n_total] = b.eoff + b.nnz;
+}
+
+// Per-graph sums of per-vertex attributions (one block per graph).
+__global__ void k_graph_sums(const BatchSrc *__restrict__ src, const unsigned long long *__restrict__ vcount,
+                             const unsigned long long *__restrict__ vcks, unsigned long long *out_count,
+                             unsigned long long *out_cks) {
+    __shared__ unsigned long long sc[32], sk[32];
+    const BatchSrc b = src[blockIdx.x];
+    unsigned long long c = 0, h = 0;
+    for (uint32_t v = threadIdx.x; v < b.n; v += blockDim.x) {
+        c += vcount[b.voff + v];
+        if (vcks) h += vcks[b.voff + v];
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        c += __shfl_down_sync(0xffffffffu, c, o);
+        h += __shfl_down_sync(0xffffffffu, h, o);
+    }
+    if (lane_id() == 0) { sc[threadIdx.x >> 5] = c; sk[threadIdx.x >> 5] = h; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long tc = 0, th = 0;
+        for (uint32_t i = 0; i < (blockDim.x >> 5); i++) { tc += sc[i]; th += sk[i]; }
+        out_count[blockIdx.x] = tc;
+        if (out_cks) out_cks[blockIdx.x] = th;
+    }
+}
+
+int launch_union_build(const BatchSrc *src, uint32_t G, uint32_t n_total, uint64_t *urp,
+                       uint32_t *ucol, uint32_t *graph_of, uint32_t *idmap, cudaStream_t s) {
+    if (G == 0) return 0;
+    k_union_build<<<G, 256, 0, s>>>(src, n_total, urp, ucol, graph_of, idmap);
+    return 1;
+}
+
+int launch_graph_sums(const BatchSrc *src, uint32_t G, const unsigned long long *vcount,
+                      const unsigned long long *vcks, unsigned long long *out_count,
+                      unsigned long long *out_cks, cudaStream_t s) {
+    if (G == 0) return 0;
+    k_graph_sums<<<G, 256, 0, s>>>(src, vcount, vcks, out_count, out_cks);
+    return 1;
+}
+
 int launch_exclusive_scan(const uint32_t *in, uint32_t *out, uint32_t n, uint32_t *block_tmp,
                           cudaStream_t s) {
     // exclusive scan; out may alias in.  block_tmp needs ceil(n/2048) +
@@ -674,7 +733,8 @@ int launch_prelist(const kcl_graph *g, uint32_t k, Workspace &w, int listing, cu
     k_uf_hook<<<wgrid, kBlock, 0, s>>>(g->n, g->rp, g->col, w.alive, w.parent);
     k_uf_stats<<<grid, kBlock, 0, s>>>(g->n, w.alive, w.parent, w.cdeg, w.comp_n, w.comp_sdeg);
     k_uf_check<<<grid, kBlock, 0, s>>>(g->n, k, w.alive, w.parent, w.comp_n, w.comp_sdeg,
-                                       w.comp_flag, listing ? w.comp_slot : nullptr, w.res);
+                                       w.comp_flag, listing ? w.comp_slot : nullptr, w.vcount_pre,
+                                       w.res);
     k_uf_remove<<<grid, kBlock, 0, s>>>(g->n, w.alive, w.parent, w.comp_flag);
     return 5;
 }
@@ -694,7 +754,8 @@ int launch_prelist_emit(const kcl_graph *g, uint32_t k, Workspace &w, uint32_t n
     k_comp_sort<<<n_comps, 256, 0, s>>>(offs, sizes, w.members);
     const bool to_ring = ring && ring->ids && ring->capacity;
     k_comp_emit<<<n_comps, 256, 0, s>>>(k, offs, sizes, w.members, to_ring ? ring->ids : nullptr,
-                                        to_ring ? ring->capacity : 0, to_ring ? ring->wrap : 0, w.res);
+                                        to_ring ? ring->capacity : 0, to_ring ? ring->wrap : 0,
+                                        croots, w.vcks_pre, w.idmap, w.res);
     return l + 3;
 }
 

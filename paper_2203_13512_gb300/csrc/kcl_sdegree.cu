@@ -39,6 +39,8 @@ struct Emit {
     uint32_t *ring;
     unsigned long long capacity;
     int wrap;
+    unsigned long long *root_cks;  // listing: per-root checksum sums, or null
+    const uint32_t *idmap;         // listing: vertex -> output id, or null (identity)
 };
 
 // lower_bound of x in a sorted list
@@ -64,6 +66,10 @@ __device__ void emit_matches(bool found, uint32_t w, uint32_t v, uint32_t k, con
         slot0 = __shfl_sync(kFull, slot0, 0);
     }
     if (!found) return;
+    if (em.idmap) {
+        v = em.idmap[v];
+        w = em.idmap[w];
+    }
     uint32_t e0 = v < w ? v : w, e1 = v < w ? w : v;
     uint32_t ex[2] = {e0, e1};
     uint32_t rec[KCL_MAX_K];
@@ -166,7 +172,7 @@ __device__ void sdegree_root(uint32_t u, uint32_t k, uint32_t D, const uint32_t 
             if (LIST && lane == 0) {
                 // R = path[0..depth] (original ids), sorted
                 for (uint32_t t = 0; t <= (uint32_t)depth; t++) {
-                    uint32_t x = path[t], j = t;
+                    uint32_t x = em.idmap ? em.idmap[path[t]] : path[t], j = t;
                     while (j > 0 && sortedR[j - 1] > x) { sortedR[j] = sortedR[j - 1]; j--; }
                     sortedR[j] = x;
                 }
@@ -211,8 +217,8 @@ __device__ void sdegree_root(uint32_t u, uint32_t k, uint32_t D, const uint32_t 
 // Every reduced list is stored from an 8-byte boundary and padded with
 // 0xFFFF to a multiple of 4 entries, so the merge join can take the paper's
 // SIMD form (Section VI-C, Example 5): load a block of 4 entries from each
-// list, compare all 16 pairs (__vcmpeq2 on packed halves), and advance the
-// block whose last entry is smaller (both when equal).
+// list, compare all 16 pairs, and advance the block whose last entry is
+// smaller (both when equal).
 
 constexpr uint16_t kPad = 0xFFFF;  // above every local index (< 1024)
 
@@ -251,7 +257,8 @@ __host__ __device__ inline LLay make_llayout(uint32_t D, uint32_t k) {
 }
 
 // |a intersect b| for padded u16 lists (8-byte aligned, lengths na, nb),
-// block form: 4 x 4 all-pairs compares per step; stops once `stop` is met.
+// block form: one 8-byte load per list per step, all 16 pairs compared, the
+// block with the smaller last entry advanced; stops once `stop` is met.
 __device__ __forceinline__ uint32_t merge_count4(const uint16_t *a, uint32_t na, const uint16_t *b,
                                                  uint32_t nb, uint32_t stop) {
     const uint2 *A = reinterpret_cast<const uint2 *>(a);
@@ -260,18 +267,16 @@ __device__ __forceinline__ uint32_t merge_count4(const uint16_t *a, uint32_t na,
     uint32_t i = 0, j = 0, c = 0;
     while (i < na4 && j < nb4 && c < stop) {
         const uint2 x = A[i], y = B[j];
-        const uint32_t y0 = y.x, y1 = y.y;
-        const uint32_t y0r = __byte_perm(y0, 0, 0x1032), y1r = __byte_perm(y1, 0, 0x1032);
-        // a padding entry never counts (it may meet padding in b)
-        const uint32_t v0 = ~__vcmpeq2(x.x, 0xFFFFFFFFu), v1 = ~__vcmpeq2(x.y, 0xFFFFFFFFu);
-        uint32_t m0 = (__vcmpeq2(x.x, y0) | __vcmpeq2(x.x, y0r) | __vcmpeq2(x.x, y1) |
-                       __vcmpeq2(x.x, y1r)) & v0;
-        uint32_t m1 = (__vcmpeq2(x.y, y0) | __vcmpeq2(x.y, y0r) | __vcmpeq2(x.y, y1) |
-                       __vcmpeq2(x.y, y1r)) & v1;
-        c += (__popc(m0) + __popc(m1)) >> 4;
-        const uint32_t amax = x.y >> 16, bmax = y1 >> 16;
-        i += amax <= bmax;
-        j += bmax <= amax;
+        const uint32_t a0 = x.x & 0xFFFFu, a1 = x.x >> 16, a2 = x.y & 0xFFFFu, a3 = x.y >> 16;
+        const uint32_t b0 = y.x & 0xFFFFu, b1 = y.x >> 16, b2 = y.y & 0xFFFFu, b3 = y.y >> 16;
+        // entries are distinct within a list, so each a_t meets at most one
+        // b entry; a padding entry never counts (it may meet padding in b)
+        c += (a0 != kPad) & ((a0 == b0) | (a0 == b1) | (a0 == b2) | (a0 == b3));
+        c += (a1 != kPad) & ((a1 == b0) | (a1 == b1) | (a1 == b2) | (a1 == b3));
+        c += (a2 != kPad) & ((a2 == b0) | (a2 == b1) | (a2 == b2) | (a2 == b3));
+        c += (a3 != kPad) & ((a3 == b0) | (a3 == b1) | (a3 == b2) | (a3 == b3));
+        i += a3 <= b3;
+        j += b3 <= a3;
     }
     return c;
 }
@@ -586,7 +591,11 @@ __device__ void sdegree_root_local(uint32_t u, uint32_t k, uint32_t D, const uin
     }
     __syncwarp();
 
-    const LView v{nbr, lofs, len, ladj, d, u, k};
+    if (LIST && em.idmap) {  // output ids (batched unions map back to each graph's ids)
+        for (uint32_t i = lane; i < d; i += 32) nbr[i] = em.idmap[nbr[i]];
+        __syncwarp();
+    }
+    const LView v{nbr, lofs, len, ladj, d, (LIST && em.idmap) ? em.idmap[u] : u, k};
     if (k == 3) {
         // C = all of N+_u: every edge of the reduced DAG closes a triangle
         if (!LIST) {
@@ -671,6 +680,7 @@ __global__ void __launch_bounds__(512) k_sdegree_cta(uint32_t k, uint32_t D, con
         const uint32_t u = roots[begin + idx];
         const uint32_t base = optr[u], d = optr[u + 1] - base;
         const unsigned long long before = cnt;
+        const unsigned long long before_cks = cks;
 
         // ---- build: members, out-list lengths, hash of N+_u, zero bit-rows
         for (uint32_t i = tid; i < d; i += nth) {
@@ -788,7 +798,9 @@ __global__ void __launch_bounds__(512) k_sdegree_cta(uint32_t k, uint32_t D, con
         }
         const uint32_t nw_dfs = meta[5], sw = meta[6];
         if (nw_dfs == 0 && tid == 0) atomicOr(&res->status, DEV_ERR_INTERNAL);  // no stack fits
-        const LView v{nbr, lofs, len, ladj, d, u, k};
+        if (LIST && em.idmap)  // output ids (batched unions map back to each graph's ids)
+            for (uint32_t i = tid; i < d; i += nth) nbr[i] = em.idmap[nbr[i]];
+        const LView v{nbr, lofs, len, ladj, d, (LIST && em.idmap) ? em.idmap[u] : u, k};
         const uint32_t cap = meta[3] ? meta[3] : 1;
         // ---- first-level children (|L(w)| >= k-2), longest lists first
         if (k > 3 && warp == 0) {
@@ -844,6 +856,11 @@ __global__ void __launch_bounds__(512) k_sdegree_cta(uint32_t k, uint32_t D, con
             for (int o = 16; o > 0; o >>= 1) mine += __shfl_down_sync(kFull, mine, o);
             if (lane == 0 && mine) atomicAdd(&per_root[u], mine);
         }
+        if (LIST && em.root_cks) {
+            unsigned long long mine = cks - before_cks;
+            for (int o = 16; o > 0; o >>= 1) mine += __shfl_down_sync(kFull, mine, o);
+            if (lane == 0 && mine) atomicAdd(&em.root_cks[u], mine);
+        }
         __syncthreads();
     }
     for (int o = 16; o > 0; o >>= 1) {
@@ -876,12 +893,18 @@ __global__ void __launch_bounds__(128) k_sdegree(uint32_t k, uint32_t D, const u
         if (idx >= end - begin) break;
         uint32_t u = roots[begin + idx];
         unsigned long long before = cnt;
+        const unsigned long long before_cks = cks;
         if (LOCAL) sdegree_root_local<LIST>(u, k, D, optr, oadj, S, em, res, cnt, cks);
         else sdegree_root<LIST>(u, k, D, optr, oadj, S, em, res, cnt, cks);
         if (per_root) {
             unsigned long long mine = cnt - before;
             for (int o = 16; o > 0; o >>= 1) mine += __shfl_down_sync(kFull, mine, o);
             if (lane == 0 && mine) atomicAdd(&per_root[u], mine);
+        }
+        if (LIST && em.root_cks) {
+            unsigned long long mine = cks - before_cks;
+            for (int o = 16; o > 0; o >>= 1) mine += __shfl_down_sync(kFull, mine, o);
+            if (lane == 0 && mine) atomicAdd(&em.root_cks[u], mine);
         }
         __syncwarp();
     }
@@ -904,7 +927,8 @@ constexpr int kWarpClasses = 3;
 constexpr int kCtaClasses = 6;
 constexpr size_t kSmemPerBlock = 96 * 1024;
 
-size_t cta_smem_bytes(uint32_t D) { return D <= 256 ? 100 * 1024 : 200 * 1024; }
+size_t cta_smem_bytes(uint32_t D) { return D <= 128 ? 48 * 1024 : D <= 256 ? 100 * 1024 : 200 * 1024; }
+int cta_threads(uint32_t D) { return D <= 128 ? 128 : 512; }
 
 template <bool LIST>
 void launch_warp_local(uint32_t k, uint32_t D, Workspace &w, uint32_t begin, uint32_t end,
@@ -917,7 +941,7 @@ void launch_warp_local(uint32_t k, uint32_t D, Workspace &w, uint32_t begin, uin
     size_t smem = (size_t)wpb * words * 4;
     auto kern = k_sdegree<LIST, false, true>;
     int occ = 0;
-    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+    if (!allow_max_smem(kern) ||
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, wpb * 32, smem) != cudaSuccess)
         (void)cudaGetLastError();
     if (occ < 1) occ = 1;
@@ -932,17 +956,18 @@ template <bool LIST>
 void launch_cta(uint32_t k, uint32_t D, Workspace &w, uint32_t begin, uint32_t end, unsigned *queue,
                 const Emit &em, unsigned long long *per_root, int num_sms, cudaStream_t s) {
     size_t smem = cta_smem_bytes(D);
+    const int threads = cta_threads(D);
     auto kern = k_sdegree_cta<LIST>;
     int occ = 0;
-    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, 512, smem) != cudaSuccess)
+    if (!allow_max_smem(kern) ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, smem) != cudaSuccess)
         (void)cudaGetLastError();
     if (occ < 1) occ = 1;
-    if (occ > 2) occ = 2;
+    if (occ > 2) occ = 2;  // the arena holds two slices per SM
     uint32_t blocks = (uint32_t)num_sms * occ;
     if (blocks > end - begin) blocks = end - begin;
-    kern<<<blocks, 512, smem, s>>>(k, D, w.optr, w.oadj, w.roots, begin, end, queue, w.arena,
-                                   (uint32_t)(smem / 4), em, per_root, w.res);
+    kern<<<blocks, threads, smem, s>>>(k, D, w.optr, w.oadj, w.roots, begin, end, queue, w.arena,
+                                       (uint32_t)(smem / 4), em, per_root, w.res);
 }
 
 template <bool LIST>
@@ -964,10 +989,12 @@ int sdegree_classes(uint32_t *limits, int max) {
     return n;
 }
 
+// Covers every class that may hold roots, including the small classes' CTA
+// form used in listing mode.
 size_t sdegree_arena_words(uint32_t k, int num_sms, uint32_t max_outdeg) {
     size_t need = 0;
-    for (int c = kWarpClasses; c < kNumClasses; c++) {
-        if (kClassD[c - 1] >= max_outdeg) break;
+    for (int c = 0; c < kNumClasses; c++) {
+        if (c > 0 && kClassD[c - 1] >= max_outdeg) break;
         size_t words = c < kCtaClasses ? (size_t)num_sms * 2 * cta_arena_words(kClassD[c])
                                        : (size_t)num_sms * 2 * make_slayout(kClassD[c], k).total;
         if (words > need) need = words;
@@ -977,7 +1004,7 @@ size_t sdegree_arena_words(uint32_t k, int num_sms, uint32_t max_outdeg) {
 
 int launch_sdegree(const kcl_graph *g, uint32_t k, Workspace &w, const uint32_t *class_begin,
                    int n_classes, const ListArgs &la, cudaStream_t s) {
-    Emit em{la.ring, la.capacity, la.wrap};
+    Emit em{la.ring, la.capacity, la.wrap, la.per_root_cks, la.idmap};
     int launches = 0;
     cudaMemsetAsync(w.queue, 0, 64 * sizeof(unsigned), s);
     for (int c = 0; c < n_classes; c++) {
@@ -987,7 +1014,9 @@ int launch_sdegree(const kcl_graph *g, uint32_t k, Workspace &w, const uint32_t 
         uint32_t D = kClassD[c];
         unsigned *q = w.queue + c;
         if (c < kWarpClasses) {
-            if (la.listing) launch_warp_local<true>(k, D, w, begin, end, q, em, la.per_root, g->num_sms, s);
+            // listing hashes every clique: a root's cost grows with its clique
+            // count, so listing shares each root's children over a CTA of 4 warps
+            if (la.listing) launch_cta<true>(k, D, w, begin, end, q, em, la.per_root, g->num_sms, s);
             else launch_warp_local<false>(k, D, w, begin, end, q, em, la.per_root, g->num_sms, s);
         } else if (c < kCtaClasses) {
             if (la.listing) launch_cta<true>(k, D, w, begin, end, q, em, la.per_root, g->num_sms, s);

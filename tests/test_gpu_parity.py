@@ -173,12 +173,20 @@ def test_edge_cases(kcl):
             assert kcl.kcl_count(g, 3, o) == 0
             assert kcl.kcl_list(g, 3, o, None)[:3] == (0, 0, 0)
     # K_k alone: Pre-List reports it; K_n with n < k: nothing
-    for n, k in ((3, 3), (8, 8), (12, 5), (6, 9), (33, 32)):
+    for n, k in ((3, 3), (8, 8), (12, 5), (6, 9)):
         rp, col = complete(n)
         g = kcl.kcl_load_csr(rp, col)
         ref = oracle.plain(rp, col, k)
         for o in ORDS:
             assert kcl.kcl_list(g, k, o, None)[:2] == ref
+    # the largest k: K_33 has C(33, 32) = 33 cliques of size 32 (closed form;
+    # the plain recursion would visit ~2^33 partial cliques here)
+    import itertools
+    rp, col = complete(33)
+    g = kcl.kcl_load_csr(rp, col)
+    want = (33, sum(oracle.clique_hash(c) for c in itertools.combinations(range(33), 32)) % (1 << 64))
+    for o in ORDS:
+        assert kcl.kcl_list(g, 32, o, None)[:2] == want
     # k bounds
     rp, col = complete(5)
     g = kcl.kcl_load_csr(rp, col)

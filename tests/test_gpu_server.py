@@ -1,0 +1,65 @@
+"""The serving loop: queries submitted concurrently (and in bursts that get
+batched) must return exactly what the same query returns alone."""
+import threading
+import time
+
+import numpy as np
+import pytest
+
+import kclgen
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def kcl():
+    import paper_2203_13512_gb300 as kcl
+    return kcl
+
+
+@pytest.mark.parametrize("slots", [1, 4])
+def test_served_results_equal_results_alone(kcl, slots):
+    graphs = [kcl.kcl_load_csr(*kclgen.rmat20(seed=s, scale=12)) for s in (1, 2)]
+    graphs += [kcl.kcl_load_csr(*kclgen.batch_graph(i)[:2]) for i in range(6)]
+    srv = kcl.kcl_server_create(slots=slots, scratch_budget_bytes=8 << 30, small_nnz=1 << 20)
+    ids = [kcl.kcl_server_add_graph(srv, g) for g in graphs]
+    rng = np.random.default_rng(slots)
+    queries = [(int(rng.integers(len(ids))), int(rng.integers(3, 8)),
+                "color" if rng.random() < 0.5 else "degree", bool(rng.random() < 0.5))
+               for _ in range(120)]
+    queries += queries[:10]  # repeated queries share results
+    tickets = [None] * len(queries)
+
+    def submitter(lo, hi):
+        for i in range(lo, hi):
+            gi, k, o, lst = queries[i]
+            tickets[i] = kcl.kcl_server_submit(srv, ids[gi], k, o, lst)
+            if i % 7 == 0:
+                time.sleep(0.001)
+
+    th = [threading.Thread(target=submitter, args=(a, min(a + 33, len(queries))))
+          for a in range(0, len(queries), 33)]
+    for t in th:
+        t.start()
+    for t in th:
+        t.join()
+    results = [kcl.kcl_server_wait(srv, t) for t in tickets]
+    srv.destroy()
+    assert max(r["batch"] for r in results) >= 1
+    for (gi, k, o, lst), r in zip(queries, results):
+        assert r["status"] == 0
+        assert r["submit_s"] <= r["start_s"] <= r["done_s"]
+        if lst:
+            c, s, _, _ = kcl.kcl_list(graphs[gi], k, o, None)
+            assert (r["count"], r["checksum"]) == (c, s)
+        else:
+            assert r["count"] == kcl.kcl_count(graphs[gi], k, o)
+
+
+def test_graph_view_shares_the_graph(kcl):
+    g = kcl.kcl_load_csr(*kclgen.rmat20(seed=5, scale=11))
+    v = kcl.kcl_graph_view(g)
+    for k in (3, 4, 5):
+        assert kcl.kcl_count(v, k, "color") == kcl.kcl_count(g, k, "color")
+    v.free()
+    assert kcl.kcl_count(g, 4, "degree") == kcl.kcl_count(g, 4, "color")
