@@ -132,8 +132,8 @@ def run_ours(args, rank, world):
                 c, s, _, _ = kcl.kcl_list(graph, k, o, None)
             total += c
             if collect is not None:
-                ms, la = kcl.kcl_last_timing(graph)
-                collect.append((k, o, mode, c, ms, la))
+                ms, la, cl = kcl.kcl_last_timing(graph)
+                collect.append((k, o, mode, c, ms, la, cl))
         return total
 
     for _ in range(args.warmup):
@@ -184,7 +184,7 @@ def run_ours(args, rank, world):
     e2e_value = (cliques // args.steps) * e2e_steps * world / (e2e_ms / 1e3)
 
     roof = roofline(per_call, args.steps)
-    launches = sum(sum(la.values()) - la["total"] for (_, _, _, _, _, la) in per_call) // args.steps
+    launches = sum(sum(pc[5].values()) - pc[5]["total"] for pc in per_call) // args.steps
     res = {
         "metric": METRIC, "value": value, "unit": "k-cliques/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": dev_ms / args.steps,
@@ -195,7 +195,7 @@ def run_ours(args, rank, world):
                    "l2": "inputs (%.0f MB CSR) larger than L2; L2 also flushed between steps"
                          % ((n + 1) * 8 / 1e6 + nnz * 4 / 1e6),
                    "parallelism": "replicas" if world > 1 else "single-gpu"},
-        "counts": {"k=%d %s %s" % (k, o, m): c for (k, o, m, c, _, _) in per_call[: len(STEP_PLAN)]},
+        "counts": {"k=%d %s %s" % pc[:3]: pc[3] for pc in per_call[: len(STEP_PLAN)]},
         "e2e": {"value": e2e_value, "unit": "k-cliques/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
@@ -209,7 +209,7 @@ def run_ours(args, rank, world):
 
 def stage_summary(per_call, steps):
     out = {}
-    for (k, o, m, c, ms, la) in per_call:
+    for (k, o, m, c, ms, la, _) in per_call:
         key = "k=%d %s %s" % (k, o, m)
         d = out.setdefault(key, {s: 0.0 for s in ms})
         for s, v in ms.items():
@@ -218,29 +218,83 @@ def stage_summary(per_call, steps):
 
 
 def roofline(per_call, steps):
-    """Dominant kernel: the listing kernels of the call family with the largest
-    device time.  Their bound is the integer pipe (AND + POPC per bitmap word,
-    or compare per merge element); the peak is derived from the SM count and
-    clock."""
+    """The dominant kernel: the single listing launch with the largest device
+    time per step -- one out-degree class of the call family whose listing
+    stage is longest.  Its bound is the integer pipe (AND + POPC per bitmap
+    word for BitCol, one compare per merge element for SDegree); the peak is
+    derived from the SM count and clock.  `achieved` = the oracle's
+    algorithmic work for the roots of that class (tests/golden/rmat20_work.json,
+    split by out-degree) / that launch's CUDA-event time."""
     peaks, src = _peaks()
     work = _load_work()
-    best = None
-    for (k, o, m, c, ms, la) in per_call:
-        key = "k=%d %s %s" % (k, o, m)
-        best = best if best and best[1] >= ms["listing"] else (key, ms["listing"], k, o, m)
-    key, _, k, o, m = best
-    times = [ms["listing"] for (kk, oo, mm, _, ms, _) in per_call if (kk, oo, mm) == (k, o, m)]
+    fam = {}
+    for (k, o, m, c, ms, la, cl) in per_call:
+        f = fam.setdefault((k, o, m), {"listing": [], "classes": {}})
+        f["listing"].append(ms["listing"])
+        for ci, cc in enumerate(cl):
+            f["classes"].setdefault((ci, cc["lo"], cc["hi"], cc["roots"]), []).append(cc["ms"])
+    (k, o, m), f = max(fam.items(), key=lambda kv: sum(kv[1]["listing"]))
+    (ci, lo, hi, roots), times = max(f["classes"].items(), key=lambda kv: sum(kv[1]))
     avg_ms = sum(times) / len(times)
     sm_mhz = peaks.get("sm_max_mhz", 2070.0)
-    # integer pipe: 16 POPC per SM per clock on 152 SMs
+    # integer pipe: 16 POPC (or ALU compare) lanes per SM sub-partition set,
+    # i.e. 16 per SM per clock, on 152 SMs
     peak_gops = 152 * 16 * sm_mhz * 1e6 / 1e9
-    wk = work.get("k=%d %s" % (k, o))
+    wk = class_work(work.get("k=%d %s" % (k, o)), lo, hi)
     achieved = (wk / (avg_ms / 1e3) / 1e9) if wk else None
-    return {"kernel": "listing kernels, %s" % key, "bound": "alu", "achieved": achieved,
-            "peak": peak_gops, "unit": "Gword/s" if o == "color" else "Gelem/s",
-            "frac": (achieved / peak_gops) if achieved else None, "traffic": None,
-            "peak_source": "derived: 152 SMs x 16 POPC/clk x %.0f MHz (%s clock)" % (sm_mhz, src),
-            "avg_ms": avg_ms}
+    kern = KERNEL_NAMES.get((o, m, ci), "listing launch of class %d" % ci)
+    tr = TRAFFIC.get((k, o, m, ci))
+    return {"kernel": "%s (k=%d %s %s, roots with %d <= d+ <= %d)" % (kern, k, o, m, lo, hi),
+            "bound": "alu", "achieved": achieved, "peak": peak_gops,
+            "unit": "Gword/s" if o == "color" else "Gelem/s",
+            "frac": (achieved / peak_gops) if achieved else None,
+            "traffic": tr[0] if tr else None,
+            "traffic_source": tr[1] if tr else None,
+            "work_per_launch": wk, "roots": roots, "avg_ms": avg_ms,
+            "listing_stage_ms": sum(f["listing"]) / len(f["listing"]),
+            "peak_source": "derived: 152 SMs x 16 POPC/clk x %.0f MHz (%s clock)" % (sm_mhz, src)}
+
+
+# listing kernels of the out-degree classes (count mode), by (ordering, mode,
+# class index); classes as in kcl_sdegree.cu / kcl_bitcol.cu
+KERNEL_NAMES = {
+    ("degree", "count", 0): "k_sdegree<0,0,1> (warp per root, d+ <= 32)",
+    ("degree", "count", 1): "k_sdegree<0,0,1> (warp per root, d+ <= 64)",
+    ("degree", "count", 2): "k_sdegree<0,0,1> (warp per root, d+ <= 128)",
+    ("degree", "count", 3): "k_sdegree_cta<0> (CTA per root, d+ <= 256)",
+    ("degree", "count", 4): "k_sdegree_cta<0> (CTA per root, d+ <= 512)",
+    ("degree", "count", 5): "k_sdegree_cta<0> (CTA per root, d+ <= 1024)",
+    ("color", "count", 0): "k_bitcol_warp<1,0>",
+    ("color", "count", 1): "k_bitcol_warp<2,0>",
+    ("color", "count", 2): "k_bitcol_warp<4,0>",
+    ("color", "count", 3): "k_bitcol_cta<8,0,0,0>",
+    ("color", "count", 4): "k_bitcol_cta<16,0,0,0>",
+    ("color", "count", 5): "k_bitcol_cta<16,0,1,0>",
+}
+
+# DRAM bytes (read + write) per launch of the dominant kernel from one ncu
+# capture of the same workload, keyed like KERNEL_NAMES plus k; the source names
+# the summary under profiles/.  Empty until a capture of the current kernel
+# exists.
+TRAFFIC = {}
+
+
+def class_work(entry, lo, hi):
+    """Oracle work of the roots with lo <= d+ <= hi, from the power-of-two
+    out-degree buckets (bucket b: 2^(b-1) < d+ <= 2^b).  Every class starts
+    just above a power of two (or at k-1, below which there are no roots) and
+    ends at one (or at the largest out-degree), so each bucket lies in one
+    class."""
+    if not entry or "work_by_outdeg" not in entry:
+        return None
+    if lo > 1 and (lo - 1) & (lo - 2) and lo - 1 > 32:
+        return None
+    total = 0
+    for b, w in entry["work_by_outdeg"].items():
+        top = 1 << int(b)
+        if top >= lo and (top >> 1) < hi:
+            total += w
+    return total
 
 
 def _load_work():
@@ -248,7 +302,7 @@ def _load_work():
     if not os.path.exists(p):
         return {}
     with open(p) as f:
-        return {k: v["work"] for k, v in json.load(f).items()}
+        return json.load(f)
 
 
 # --------------------------------------------------------- oracle (CPU)

@@ -197,11 +197,22 @@ void kcl_server_destroy(kcl_server *s);
  * milliseconds, measured with CUDA events on the graph's stream when timing
  * is enabled (kcl_enable_timing).  stage ids: 0 Pre-Core, 1 Pre-List,
  * 2 orientation, 3 listing kernels (SDegreeList / subgraph build + BitColList),
- * 4 whole call.  launches[i] = kernel launches in stage i. */
+ * 4 whole call.  launches[i] = kernel launches in stage i.
+ * The listing stage is split by root class: the roots are grouped by their
+ * out-degree d+_u (one listing launch per non-empty group), and for c <
+ * n_classes group c holds class_roots[c] roots with class_lo[c] <= d+_u <=
+ * class_hi[c], listed by one launch that took class_ms[c] milliseconds
+ * (0 roots: no launch, class_ms[c] = 0).  Batches leave n_classes = 0. */
 #define KCL_NUM_STAGES 5
+#define KCL_MAX_CLASSES 16
 typedef struct {
     float ms[KCL_NUM_STAGES];
     uint32_t launches[KCL_NUM_STAGES];
+    uint32_t n_classes;
+    uint32_t class_lo[KCL_MAX_CLASSES];
+    uint32_t class_hi[KCL_MAX_CLASSES];
+    uint32_t class_roots[KCL_MAX_CLASSES];
+    float class_ms[KCL_MAX_CLASSES];
 } kcl_timing;
 kcl_status kcl_enable_timing(kcl_graph *g, int enable);
 kcl_status kcl_last_timing(const kcl_graph *g, kcl_timing *t);

@@ -29,6 +29,7 @@ KCL_ETIMEOUT, KCL_ECUDA, KCL_EABORT, KCL_ELIMIT = 5, 6, 7, 8
 KCL_ORDER_DEGREE, KCL_ORDER_COLOR = 0, 1
 KCL_MAX_K = 32
 KCL_NUM_STAGES = 5
+KCL_MAX_CLASSES = 16
 STAGES = ("pre_core", "pre_list", "orientation", "listing", "total")
 ORDERINGS = {"degree": KCL_ORDER_DEGREE, "color": KCL_ORDER_COLOR,
              "sdegree": KCL_ORDER_DEGREE, "bitcol": KCL_ORDER_COLOR}
@@ -47,7 +48,17 @@ class _Ring(ctypes.Structure):
 
 class _Timing(ctypes.Structure):
     _fields_ = [("ms", ctypes.c_float * KCL_NUM_STAGES),
-                ("launches", ctypes.c_uint32 * KCL_NUM_STAGES)]
+                ("launches", ctypes.c_uint32 * KCL_NUM_STAGES),
+                ("n_classes", ctypes.c_uint32),
+                ("class_lo", ctypes.c_uint32 * KCL_MAX_CLASSES),
+                ("class_hi", ctypes.c_uint32 * KCL_MAX_CLASSES),
+                ("class_roots", ctypes.c_uint32 * KCL_MAX_CLASSES),
+                ("class_ms", ctypes.c_float * KCL_MAX_CLASSES)]
+
+    def classes(self):
+        return [{"lo": int(self.class_lo[c]), "hi": int(self.class_hi[c]),
+                 "roots": int(self.class_roots[c]), "ms": float(self.class_ms[c])}
+                for c in range(min(int(self.n_classes), KCL_MAX_CLASSES))]
 
 
 _P, _U32, _U64, _I = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int
@@ -236,7 +247,7 @@ def kcl_last_timing(g):
     t = _Timing()
     _check(_lib.kcl_last_timing(g.handle, ctypes.byref(t)), "kcl_last_timing")
     return ({STAGES[i]: float(t.ms[i]) for i in range(KCL_NUM_STAGES)},
-            {STAGES[i]: int(t.launches[i]) for i in range(KCL_NUM_STAGES)})
+            {STAGES[i]: int(t.launches[i]) for i in range(KCL_NUM_STAGES)}, t.classes())
 
 
 def kcl_strerror(status):

@@ -164,6 +164,7 @@ struct StageTimer {
             g->timing.ms[i] = 0.f;
             g->timing.launches[i] = 0;
         }
+        g->timing.n_classes = 0;
     }
     void mark(int idx) {
         if (g->timing.enabled) cudaEventRecord(g->timing.ev[idx], g->stream);
@@ -174,13 +175,31 @@ struct StageTimer {
     void collect() {
         if (!g->timing.enabled) return;
         cudaStreamSynchronize(g->stream);
-        for (int i = 0; i < KCL_NUM_STAGES; i++) {
-            float ms = 0.f;
-            if (cudaEventElapsedTime(&ms, g->timing.ev[2 * i], g->timing.ev[2 * i + 1]) == cudaSuccess)
-                g->timing.ms[i] = ms;
-            else
-                (void)cudaGetLastError();
+        for (int i = 0; i < KCL_NUM_STAGES; i++) g->timing.ms[i] = elapsed(g->timing.ev + 2 * i);
+    }
+    // per-class split of the listing stage; class c holds root positions
+    // [class_begin[c], class_begin[c-1]) (roots sorted by d+ descending)
+    void collect_classes(uint32_t k, const uint32_t *class_begin, const uint32_t *limits, int n,
+                         uint32_t max_outdeg) {
+        Timing &t = g->timing;
+        t.n_classes = 0;
+        if (!t.enabled || n > KCL_MAX_CLASSES) return;
+        t.n_classes = (uint32_t)n;
+        for (int c = 0; c < n; c++) {
+            const uint32_t end = c ? class_begin[c - 1] : class_begin[n];
+            t.class_lo[c] = c ? limits[c - 1] + 1 : k - 1;
+            t.class_hi[c] = std::min(limits[c], max_outdeg);
+            t.class_roots[c] = end > class_begin[c] ? end - class_begin[c] : 0;
+            t.class_ms[c] = t.class_roots[c] ? elapsed(t.cev + 2 * c) : 0.f;
         }
+    }
+    static float elapsed(const cudaEvent_t *ev) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, ev[0], ev[1]) != cudaSuccess) {
+            (void)cudaGetLastError();
+            ms = 0.f;
+        }
+        return ms;
     }
 };
 
@@ -188,6 +207,7 @@ struct FrontEnd {
     uint32_t max_outdeg = 0;
     uint32_t n_roots = 0;
     uint32_t class_begin[17] = {};
+    uint32_t limits[16] = {};  // class c: d+ <= limits[c]
     int n_classes = 0;
     unsigned long long pre_count = 0;
 };
@@ -293,7 +313,7 @@ kcl_status run_front(kcl_graph *g, uint32_t k, kcl_ordering ord, const kcl_ring 
     KCL_CK(cudaMemsetAsync(&w.res->max_outdeg, 0, sizeof(unsigned), s));
     T.add(2, launch_orient(g, k, w, s));
     KCL_TRY(read_u32(g, &w.res->max_outdeg, &fe.max_outdeg));
-    uint32_t limits[16];
+    uint32_t *limits = fe.limits;
     fe.n_classes = ord == KCL_ORDER_DEGREE ? sdegree_classes(limits, 16) : bitcol_classes(limits, 16);
     T.add(2, launch_roots(g, k, w, fe.max_outdeg, fe.class_begin, limits, fe.n_classes, s));
     T.end(2);
@@ -331,6 +351,7 @@ kcl_status run_call(kcl_graph *g, uint32_t k, kcl_ordering ord, const kcl_ring *
     la.per_root = per_root;
     la.per_root_cks = listing ? per_root_cks : nullptr;
     la.idmap = idmap;
+    if (g->timing.enabled) la.class_ev = g->timing.cev;
     if (listing && ring) {
         la.ring = ring->capacity ? ring->ids : nullptr;
         la.capacity = ring->capacity;
@@ -352,6 +373,7 @@ kcl_status run_call(kcl_graph *g, uint32_t k, kcl_ordering ord, const kcl_ring *
     KCL_CK(cudaGetLastError());
     KCL_TRY(read_result(g));
     T.collect();
+    if (fe.n_roots > 0) T.collect_classes(k, fe.class_begin, fe.limits, fe.n_classes, fe.max_outdeg);
     if (w.h_res->status) return status_from_device(w.h_res->status);
     return KCL_OK;
 }
@@ -545,6 +567,8 @@ void kcl_free_graph(kcl_graph *g) {
     if (g->owns_csr && g->col) cudaFree(g->col);
     for (int i = 0; i < 2 * KCL_NUM_STAGES; i++)
         if (g->timing.ev[i]) cudaEventDestroy(g->timing.ev[i]);
+    for (int i = 0; i < 2 * KCL_MAX_CLASSES; i++)
+        if (g->timing.cev[i]) cudaEventDestroy(g->timing.cev[i]);
     (void)cudaGetLastError();
     delete g;
 }
@@ -700,6 +724,11 @@ kcl_status kcl_enable_timing(kcl_graph *g, int enable) {
                 (void)cudaGetLastError();
                 return KCL_ECUDA;
             }
+        for (int i = 0; i < 2 * KCL_MAX_CLASSES; i++)
+            if (cudaEventCreate(&g->timing.cev[i]) != cudaSuccess) {
+                (void)cudaGetLastError();
+                return KCL_ECUDA;
+            }
     }
     g->timing.enabled = enable ? 1 : 0;
     return KCL_OK;
@@ -707,9 +736,17 @@ kcl_status kcl_enable_timing(kcl_graph *g, int enable) {
 
 kcl_status kcl_last_timing(const kcl_graph *g, kcl_timing *t) {
     if (!g || !t) return KCL_EINVAL;
+    *t = kcl_timing{};
     for (int i = 0; i < KCL_NUM_STAGES; i++) {
         t->ms[i] = g->timing.ms[i];
         t->launches[i] = g->timing.launches[i];
+    }
+    t->n_classes = g->timing.n_classes;
+    for (uint32_t c = 0; c < g->timing.n_classes; c++) {
+        t->class_lo[c] = g->timing.class_lo[c];
+        t->class_hi[c] = g->timing.class_hi[c];
+        t->class_roots[c] = g->timing.class_roots[c];
+        t->class_ms[c] = g->timing.class_ms[c];
     }
     return KCL_OK;
 }

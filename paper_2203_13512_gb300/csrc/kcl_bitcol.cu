@@ -764,6 +764,7 @@ int launch_bitcol(const kcl_graph *g, uint32_t k, Workspace &w, const uint32_t *
         const ClassCfg &cc = kClass[c];
         unsigned *q = w.queue + c;
         const size_t smem = class_smem(c, k);
+        class_mark(la, c, 0, s);
         if (!cc.cta && la.listing) {
             // listing: every clique is hashed one by one, so a root's cost grows
             // with its clique count; a CTA of 4 warps shares each root's
@@ -795,6 +796,7 @@ int launch_bitcol(const kcl_graph *g, uint32_t k, Workspace &w, const uint32_t *
             else { KCL_C(2, true, true) }
 #undef KCL_C
         }
+        class_mark(la, c, 1, s);
         launches++;
     }
     return launches;

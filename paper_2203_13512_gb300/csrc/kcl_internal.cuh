@@ -93,8 +93,13 @@ struct Workspace {
 struct Timing {
     int enabled = 0;
     cudaEvent_t ev[2 * KCL_NUM_STAGES] = {};
+    cudaEvent_t cev[2 * KCL_MAX_CLASSES] = {};  // around each class's listing launch
     float ms[KCL_NUM_STAGES] = {};
     uint32_t launches[KCL_NUM_STAGES] = {};
+    uint32_t n_classes = 0;
+    uint32_t class_lo[KCL_MAX_CLASSES] = {}, class_hi[KCL_MAX_CLASSES] = {};
+    uint32_t class_roots[KCL_MAX_CLASSES] = {};
+    float class_ms[KCL_MAX_CLASSES] = {};
 };
 
 }  // namespace kcl
@@ -260,7 +265,12 @@ struct ListArgs {
     unsigned long long *per_root = nullptr;
     unsigned long long *per_root_cks = nullptr;  // listing: checksum per root
     const uint32_t *idmap = nullptr;             // listing: vertex -> output id
+    cudaEvent_t *class_ev = nullptr;             // timing: 2 events per class, or null
 };
+// Records class_ev[2c] / [2c+1] (when timing) around the launch of class c.
+inline void class_mark(const ListArgs &la, int c, int end, cudaStream_t s) {
+    if (la.class_ev) cudaEventRecord(la.class_ev[2 * c + end], s);
+}
 int bitcol_classes(uint32_t *limits, int max);
 int launch_bitcol(const kcl_graph *g, uint32_t k, Workspace &w, const uint32_t *class_begin,
                   int n_classes, const ListArgs &la, cudaStream_t s);

@@ -1013,6 +1013,7 @@ int launch_sdegree(const kcl_graph *g, uint32_t k, Workspace &w, const uint32_t 
         if (end <= begin) continue;
         uint32_t D = kClassD[c];
         unsigned *q = w.queue + c;
+        class_mark(la, c, 0, s);
         if (c < kWarpClasses) {
             // listing hashes every clique: a root's cost grows with its clique
             // count, so listing shares each root's children over a CTA of 4 warps
@@ -1025,6 +1026,7 @@ int launch_sdegree(const kcl_graph *g, uint32_t k, Workspace &w, const uint32_t 
             if (la.listing) launch_global_lists<true>(k, D, w, begin, end, q, em, la.per_root, g->num_sms, s);
             else launch_global_lists<false>(k, D, w, begin, end, q, em, la.per_root, g->num_sms, s);
         }
+        class_mark(la, c, 1, s);
         launches++;
     }
     return launches;

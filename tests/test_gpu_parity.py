@@ -142,6 +142,31 @@ def test_planted_communities_span_the_classes(kcl, size, p):
             assert (c, s) == ref, (k, ordering)
 
 
+@pytest.mark.parametrize("ordering", ORDS)
+def test_class_timing_matches_oracle_outdegrees(kcl, ordering):
+    """The per-class split of the listing stage (used to attribute the
+    oracle's per-out-degree work to one launch) covers exactly the roots the
+    oracle expands, class by class."""
+    rp, col = kclgen.chung_lu(3000, 12000, 2.3, groups=3, group_size=(260, 260), group_p=0.45,
+                              seed=260)
+    g = kcl.kcl_load_csr(rp, col)
+    kcl.kcl_enable_timing(g, True)
+    for k in (3, 5):
+        kcl.kcl_count(g, k, ordering)
+        ms, la, classes = kcl.kcl_last_timing(g)
+        pl = oracle.prelist(rp, col, k, oracle.precore(rp, col, k))
+        od = oracle.outdegrees(rp, col, pl["alive"], 0 if ordering == "degree" else 1).astype(np.int64)
+        od = od[(pl["alive"] != 0) & (od >= k - 1)]
+        assert classes and sum(c["roots"] for c in classes) == len(od)
+        launched = 0
+        for c in classes:
+            assert c["roots"] == int(np.count_nonzero((od >= c["lo"]) & (od <= c["hi"])))
+            assert (c["ms"] > 0) == (c["roots"] > 0)
+            launched += c["roots"] > 0
+        assert launched == la["listing"]
+        assert sum(c["ms"] for c in classes) <= ms["listing"] * 1.01 + 0.05
+
+
 def _near_complete(n):
     """K_n minus the edge {0, 1}: C(n,k) - C(n-2,k-2) k-cliques, and no
     Pre-List shortcut (the component is not a clique)."""
