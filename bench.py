@@ -175,10 +175,7 @@ def run_ours(args, rank, world):
     h2d = (n + 1) * 8 + nnz * 4
     d2h = 16 * len(STEP_PLAN)
 
-    if world > 1:
-        t = torch.tensor([dev_ms, e2e_ms], dtype=torch.float64, device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        dev_ms, e2e_ms = float(t[0]), float(t[1])
+    dev_ms, e2e_ms = max_over_ranks([dev_ms, e2e_ms], world)
     cliques_all = cliques * world
     value = cliques_all / (dev_ms / 1e3)
     e2e_value = (cliques // args.steps) * e2e_steps * world / (e2e_ms / 1e3)
@@ -207,14 +204,37 @@ def run_ours(args, rank, world):
     return res
 
 
+def max_over_ranks(values, world):
+    """Element-wise maximum of per-rank floats over the job (the slowest
+    replica's times); the identity for one rank."""
+    if world <= 1:
+        return list(values)
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor(list(values), dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(x) for x in t.cpu()]
+
+
 def stage_summary(per_call, steps):
-    out = {}
-    for (k, o, m, c, ms, la, _) in per_call:
+    """Mean stage times per call family, and the listing stage split by
+    out-degree class: [lo, hi, roots, ms] for each launched class."""
+    out, cls = {}, {}
+    for (k, o, m, c, ms, la, cl) in per_call:
         key = "k=%d %s %s" % (k, o, m)
         d = out.setdefault(key, {s: 0.0 for s in ms})
         for s, v in ms.items():
             d[s] += v / steps
-    return {k: {s: round(v, 3) for s, v in d.items()} for k, d in out.items()}
+        cc = cls.setdefault(key, {})
+        for x in cl:
+            if x["roots"]:
+                cc.setdefault((x["lo"], x["hi"], x["roots"]), []).append(x["ms"])
+    res = {k: {s: round(v, 3) for s, v in d.items()} for k, d in out.items()}
+    for key, cc in cls.items():
+        res[key]["classes"] = [[lo, hi, r, round(sum(t) / len(t), 3)]
+                               for (lo, hi, r), t in sorted(cc.items())]
+    return res
 
 
 def roofline(per_call, steps):
@@ -237,9 +257,11 @@ def roofline(per_call, steps):
     (ci, lo, hi, roots), times = max(f["classes"].items(), key=lambda kv: sum(kv[1]))
     avg_ms = sum(times) / len(times)
     sm_mhz = peaks.get("sm_max_mhz", 2070.0)
-    # integer pipe: 16 POPC (or ALU compare) lanes per SM sub-partition set,
-    # i.e. 16 per SM per clock, on 152 SMs
-    peak_gops = 152 * 16 * sm_mhz * 1e6 / 1e9
+    # integer pipe per SM and clock: 16 POPC (BitCol: one AND + POPC per
+    # bitmap word, POPC-limited) or 64 32-bit compares (SDegree: at least one
+    # compare per merge element), on 152 SMs
+    per_clk = 16 if o == "color" else 64
+    peak_gops = 152 * per_clk * sm_mhz * 1e6 / 1e9
     wk = class_work(work.get("k=%d %s" % (k, o)), lo, hi)
     achieved = (wk / (avg_ms / 1e3) / 1e9) if wk else None
     kern = KERNEL_NAMES.get((o, m, ci), "listing launch of class %d" % ci)
@@ -252,7 +274,8 @@ def roofline(per_call, steps):
             "traffic_source": tr[1] if tr else None,
             "work_per_launch": wk, "roots": roots, "avg_ms": avg_ms,
             "listing_stage_ms": sum(f["listing"]) / len(f["listing"]),
-            "peak_source": "derived: 152 SMs x 16 POPC/clk x %.0f MHz (%s clock)" % (sm_mhz, src)}
+            "peak_source": "derived: 152 SMs x %d %s/clk x %.0f MHz (%s clock)"
+                           % (per_clk, "POPC" if o == "color" else "compares", sm_mhz, src)}
 
 
 # listing kernels of the out-degree classes (count mode), by (ordering, mode,
@@ -419,7 +442,7 @@ def run_batch(args):
 # ------------------------------------------------------- served form
 def run_serve(args):
     """The served workload: 64 resident graphs -- ids 1-32 R-MAT at scale
-    12 + (id mod 5), ids 33-64 graph `id` of the batched workload -- and a
+    10 + (id mod 5), ids 33-64 graph `id` of the batched workload -- and a
     Poisson stream of (graph, k in 3..8, count | count + checksum) queries
     (seed 1).  The server (8 slots, 100 GB scratch budget, continuous
     batching) is compared with a FIFO loop that runs one query at a time in
@@ -429,7 +452,7 @@ def run_serve(args):
 
     import kclgen
     import paper_2203_13512_gb300 as kcl
-    graphs = [kcl.kcl_load_csr(*kclgen.rmat20(seed=i, scale=12 + i % 5)) for i in range(1, 33)]
+    graphs = [kcl.kcl_load_csr(*kclgen.rmat20(seed=i, scale=10 + i % 5)) for i in range(1, 33)]
     graphs += [kcl.kcl_load_csr(*kclgen.batch_graph(i)[:2]) for i in range(33, 65)]
     rng = np.random.default_rng(1)
     Q = args.serve_queries
@@ -448,17 +471,26 @@ def run_serve(args):
     for q in qs[:64]:
         run_one(q)  # warm-up
     service, ref = [], []
-    for q in qs:
+    t_fifo = time.perf_counter()
+    for qi, q in enumerate(qs):
         torch.cuda.synchronize()
         t = time.perf_counter()
         ref.append(run_one(q))
         service.append(time.perf_counter() - t)
+        if qi % 500 == 499:
+            print("fifo %d queries, %.1f s" % (qi + 1, time.perf_counter() - t_fifo),
+                  file=sys.stderr, flush=True)
     out = {"metric": "served queries: throughput and latency, continuous batching vs FIFO",
            "unit": "queries/s", "higher_is_better": True, "n_gpus": 1,
            "config": {"workload": "served-mixed", "graphs": 64, "queries": Q,
-                      "rmat_scales": "12..16", "k": "3..8", "slots": 8,
+                      "rmat_scales": "10..14", "k": "3..8", "slots": 8,
                       "scratch_budget_gb": 100},
-           "data": "synthetic", "rates": {}}
+           "data": "synthetic", "rates": {},
+           "service_ms": {"p50": 1e3 * float(np.percentile(service, 50)),
+                          "p99": 1e3 * float(np.percentile(service, 99)),
+                          "max": 1e3 * float(max(service)), "sum_s": float(sum(service))},
+           "slowest": [list(qs[i]) + [round(1e3 * service[i], 2)]
+                       for i in np.argsort(service)[::-1][:5]]}
     for rate in args.serve_rates:
         arr = np.cumsum(gaps / rate)
         done, lat = 0.0, []
@@ -479,6 +511,7 @@ def run_serve(args):
             tickets.append(kcl.kcl_server_submit(srv, ids[gi], k, o, lst))
         res = [kcl.kcl_server_wait(srv, t) for t in tickets]
         srv.destroy()
+        print("served at %g/s" % rate, file=sys.stderr, flush=True)
         for r, want, q in zip(res, ref, qs):
             assert r["status"] == 0 and (r["count"], r["checksum"]) == want, q
         slat = [r["done_s"] - r["submit_s"] for r in res]
@@ -522,7 +555,7 @@ def main():
                     help="single: the R-MAT scale-20 line; batch / serve: the batched and "
                          "served workloads, each printing its own JSON line")
     ap.add_argument("--batch-graphs", type=int, default=512)
-    ap.add_argument("--serve-queries", type=int, default=4000)
+    ap.add_argument("--serve-queries", type=int, default=2000)
     ap.add_argument("--serve-rates", type=float, nargs="+", default=[1000.0, 10000.0])
     ap.add_argument("--profile-case", default=None,
                     help="SCALE:K:ORDERING[:count|list] -- one call on R-MAT at SCALE "
