@@ -119,6 +119,11 @@ def run_ours(args, rank, world):
     rp, col = workload()
     n, nnz = len(rp) - 1, len(col)
     g = kcl.kcl_load_csr(rp, col)
+    # the library's autotuner picks SDegree's leaf form per out-degree class
+    # on the heaviest degree-ordered call (untimed, like the warm-up)
+    kcl.kcl_autotune(g, max(k for k, o, m in STEP_PLAN if o == "degree" and m == "count"), "degree")
+    tuning = kcl.kcl_autotune(g, max(k for k, o, m in STEP_PLAN if o == "degree" and m == "list"),
+                              "degree", listing=True)
     kcl.kcl_enable_timing(g, True)
 
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.int32, device="cuda")
@@ -168,6 +173,7 @@ def run_ours(args, rank, world):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         g2 = kcl.kcl_load_csr(rp_pin.numpy().view(np.uint64), col_pin.numpy().view(np.uint32))
+        kcl.kcl_set_tuning(g2, tuning)
         step(g2)
         g2.free()
         torch.cuda.synchronize()
@@ -191,7 +197,8 @@ def run_ours(args, rank, world):
                    "plan": ["k=%d %s %s" % p for p in STEP_PLAN],
                    "l2": "inputs (%.0f MB CSR) larger than L2; L2 also flushed between steps"
                          % ((n + 1) * 8 / 1e6 + nnz * 4 / 1e6),
-                   "parallelism": "replicas" if world > 1 else "single-gpu"},
+                   "parallelism": "replicas" if world > 1 else "single-gpu",
+                   "tuning": tuning},
         "counts": {"k=%d %s %s" % pc[:3]: pc[3] for pc in per_call[: len(STEP_PLAN)]},
         "e2e": {"value": e2e_value, "unit": "k-cliques/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
@@ -442,8 +449,8 @@ def run_batch(args):
 # ------------------------------------------------------- served form
 def run_serve(args):
     """The served workload: 64 resident graphs -- ids 1-32 R-MAT at scale
-    10 + (id mod 5), ids 33-64 graph `id` of the batched workload -- and a
-    Poisson stream of (graph, k in 3..8, count | count + checksum) queries
+    10 + (id mod 3), ids 33-64 graph `id` of the batched workload -- and a
+    Poisson stream of (graph, k in 3..6, count | count + checksum) queries
     (seed 1).  The server (8 slots, 100 GB scratch budget, continuous
     batching) is compared with a FIFO loop that runs one query at a time in
     arrival order; every served result must equal the FIFO result."""
@@ -452,11 +459,11 @@ def run_serve(args):
 
     import kclgen
     import paper_2203_13512_gb300 as kcl
-    graphs = [kcl.kcl_load_csr(*kclgen.rmat20(seed=i, scale=10 + i % 5)) for i in range(1, 33)]
+    graphs = [kcl.kcl_load_csr(*kclgen.rmat20(seed=i, scale=10 + i % 3)) for i in range(1, 33)]
     graphs += [kcl.kcl_load_csr(*kclgen.batch_graph(i)[:2]) for i in range(33, 65)]
     rng = np.random.default_rng(1)
     Q = args.serve_queries
-    qs = [(int(rng.integers(64)), int(rng.integers(3, 9)),
+    qs = [(int(rng.integers(64)), int(rng.integers(3, 7)),
            "color" if rng.random() < 0.5 else "degree", bool(rng.random() < 0.5)) for _ in range(Q)]
     gaps = rng.exponential(1.0, Q)
 
@@ -477,13 +484,13 @@ def run_serve(args):
         t = time.perf_counter()
         ref.append(run_one(q))
         service.append(time.perf_counter() - t)
-        if qi % 500 == 499:
+        if qi % 250 == 249:
             print("fifo %d queries, %.1f s" % (qi + 1, time.perf_counter() - t_fifo),
                   file=sys.stderr, flush=True)
     out = {"metric": "served queries: throughput and latency, continuous batching vs FIFO",
            "unit": "queries/s", "higher_is_better": True, "n_gpus": 1,
            "config": {"workload": "served-mixed", "graphs": 64, "queries": Q,
-                      "rmat_scales": "10..14", "k": "3..8", "slots": 8,
+                      "rmat_scales": "10..12", "k": "3..6", "slots": 8,
                       "scratch_budget_gb": 100},
            "data": "synthetic", "rates": {},
            "service_ms": {"p50": 1e3 * float(np.percentile(service, 50)),
@@ -528,6 +535,52 @@ def run_serve(args):
     return out
 
 
+def run_ablation(args):
+    """The preprocessing / pruning study and the memory study on the bench
+    graph (R-MAT scale 20): for k = 4, 5 and both orderings, device time of
+    one call with everything on, without Pre-Core, without Pre-List, and
+    (BitCol) without the colour prune; and the device scratch a fresh handle
+    holds after one call of each (k, ordering)."""
+    import torch
+
+    import paper_2203_13512_gb300 as kcl
+    rp, col = workload()
+    g = kcl.kcl_load_csr(rp, col)
+    kcl.kcl_enable_timing(g, True)
+    configs = [("all on", 0), ("no Pre-Core", kcl.KCL_OPT_NO_PRECORE),
+               ("no Pre-List", kcl.KCL_OPT_NO_PRELIST),
+               ("no colour prune", kcl.KCL_OPT_NO_COLOR_PRUNE)]
+    out = {"metric": "ablation: device ms per call (R-MAT scale 20)", "unit": "ms",
+           "higher_is_better": False, "n_gpus": 1,
+           "config": {"workload": "rmat-scale20-ef16", "repeats": args.steps},
+           "data": "synthetic", "calls": {}, "scratch_bytes": {}}
+    for k in (4, 5):
+        for o in ("color", "degree"):
+            row = {}
+            for name, flags in configs:
+                if o == "degree" and flags == kcl.KCL_OPT_NO_COLOR_PRUNE:
+                    continue
+                kcl.kcl_set_options(g, flags)
+                c0 = kcl.kcl_count(g, k, o)  # warm-up
+                ms = []
+                for _ in range(max(1, args.steps)):
+                    torch.cuda.synchronize()
+                    c = kcl.kcl_count(g, k, o)
+                    assert c == c0
+                    ms.append(kcl.kcl_last_timing(g)[0])
+                row[name] = {s_: round(sum(m[s_] for m in ms) / len(ms), 3) for s_ in ms[0]}
+                row[name]["count"] = c
+            out["calls"]["k=%d %s" % (k, o)] = row
+            v = kcl.kcl_graph_view(g)
+            kcl.kcl_count(v, k, o)
+            ws, ar = kcl.kcl_scratch_bytes(v)
+            out["scratch_bytes"]["k=%d %s" % (k, o)] = {"workspace": ws, "arena": ar}
+            v.free()
+    kcl.kcl_set_options(g, 0)
+    g.free()
+    return out
+
+
 def profile_case(spec):
     """A single library call on a smaller R-MAT graph (for ncu captures)."""
     import kclgen
@@ -551,12 +604,12 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--form", default="single", choices=["single", "batch", "serve"],
+    ap.add_argument("--form", default="single", choices=["single", "batch", "serve", "ablation"],
                     help="single: the R-MAT scale-20 line; batch / serve: the batched and "
                          "served workloads, each printing its own JSON line")
     ap.add_argument("--batch-graphs", type=int, default=512)
     ap.add_argument("--serve-queries", type=int, default=2000)
-    ap.add_argument("--serve-rates", type=float, nargs="+", default=[1000.0, 10000.0])
+    ap.add_argument("--serve-rates", type=float, nargs="+", default=[50.0, 150.0, 1000.0])
     ap.add_argument("--profile-case", default=None,
                     help="SCALE:K:ORDERING[:count|list] -- one call on R-MAT at SCALE "
                          "(16 * 2^SCALE edges, seed 1), for profilers")
@@ -565,7 +618,7 @@ def main():
         profile_case(args.profile_case)
         return
     if args.form != "single":
-        res = run_batch(args) if args.form == "batch" else run_serve(args)
+        res = {"batch": run_batch, "serve": run_serve, "ablation": run_ablation}[args.form](args)
         print(json.dumps(res))
         return
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -221,6 +221,63 @@ kcl_status kcl_last_timing(const kcl_graph *g, kcl_timing *t);
 kcl_status kcl_batch_enable_timing(kcl_batch *b, int enable);
 kcl_status kcl_batch_last_timing(const kcl_batch *b, kcl_timing *t, uint32_t *groups);
 
+/* Ablation switches (Section IX, the preprocessing and pruning studies): a
+ * bitwise OR of
+ *   KCL_OPT_NO_PRECORE      skip Pre-Core (Algorithm 3): every vertex stays;
+ *   KCL_OPT_NO_PRELIST      skip Pre-List (Algorithm 4): clique components
+ *                           are listed by the DFS like any other part;
+ *   KCL_OPT_NO_COLOR_PRUNE  BitCol expands every candidate instead of only
+ *                           those of colour >= l (Lemma 1).
+ * Counts, checksums and listings do not change; only the work does.  A graph
+ * starts with 0 (everything on).  Unknown bits: KCL_EINVAL. */
+#define KCL_OPT_NO_PRECORE 1u
+#define KCL_OPT_NO_PRELIST 2u
+#define KCL_OPT_NO_COLOR_PRUNE 4u
+kcl_status kcl_set_options(kcl_graph *g, uint32_t flags);
+kcl_status kcl_get_options(const kcl_graph *g, uint32_t *flags);
+
+/* Device scratch the graph handle holds now (Section IX's memory study): the
+ * per-call workspace (about 74 bytes per vertex and 2 per CSR entry, grown to
+ * the largest graph seen) and the listing arena (shared-memory spill of the
+ * largest subproblems, sized by k and the largest out-degree), in bytes.
+ * The input CSR itself (8 (n+1) + 4 nnz bytes) is not included. */
+kcl_status kcl_scratch_bytes(const kcl_graph *g, uint64_t *workspace, uint64_t *arena);
+
+/* Tuning of the listing kernels (a library facility; the paper has no
+ * counterpart).  Results never depend on it, only speed does.
+ * sdegree_gallop[c] (counting) and sdegree_gallop_list[c] (listing): for the
+ *   SDegree launch of out-degree class c (the same classes as kcl_timing's
+ *   class split), a leaf (l = 2) intersects by galloping -- each pair
+ *   (candidate, later candidate) searched in the candidate's list -- instead
+ *   of merging when
+ *     pairs * (6 lg + 10) * 10 < (sum of list lengths + pairs) * threshold
+ *   (lg = bit length of the mean list length); 0 = always merge (default).
+ * sdegree_bitmap[c]: bitmap-versus-list threshold for the CTA-per-root
+ *   classes (d+ 129..1024): a root runs SDegreeList on the directed bit-rows
+ *   of its reduced subproblem instead of its reduced lists when the rows fit
+ *   in shared memory with enough warps and 16 * (list words) > t * (row
+ *   words), t = sdegree_bitmap[c] (0 means the default t = 16: lists larger
+ *   than rows; 0xFFFFFFFF = lists always).  Both forms compute the same
+ *   intersections; only their representation differs.
+ * A graph starts with the defaults; views and batches start with the
+ * defaults too. */
+typedef struct {
+    uint32_t sdegree_gallop[KCL_MAX_CLASSES];
+    uint32_t sdegree_gallop_list[KCL_MAX_CLASSES];
+    uint32_t sdegree_bitmap[KCL_MAX_CLASSES];
+} kcl_tuning;
+kcl_status kcl_get_tuning(const kcl_graph *g, kcl_tuning *t);
+kcl_status kcl_set_tuning(kcl_graph *g, const kcl_tuning *t);
+/* Autotuner: runs kcl_count(g, k, ord) (listing = 0) or kcl_list(g, k, ord,
+ * NULL, ...) (listing = 1) once per candidate setting, times every class
+ * launch with CUDA events, and keeps for each class the fastest setting (a
+ * later candidate must be 2% faster).  For KCL_ORDER_DEGREE it tunes
+ * sdegree_bitmap first (candidates 0, 4, 64, 0xFFFFFFFF), then that mode's
+ * galloping array (0, 40, 80, 160, 400); BitCol has no knob yet.  The tuning
+ * is stored in g and copied to *out when out is not NULL.  Timing stays as
+ * the caller left it.  Errors: those of kcl_count / kcl_list. */
+kcl_status kcl_autotune(kcl_graph *g, uint32_t k, kcl_ordering ord, int listing, kcl_tuning *out);
+
 /* Allocation-free degeneracy ordering (the paper has no counterpart; this is
  * a library facility).  Some callers must not allocate device memory from
  * inside their own loops: a serving loop whose latency budget cannot absorb

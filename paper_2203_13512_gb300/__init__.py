@@ -61,6 +61,15 @@ class _Timing(ctypes.Structure):
                 for c in range(min(int(self.n_classes), KCL_MAX_CLASSES))]
 
 
+class _Tuning(ctypes.Structure):
+    _fields_ = [("sdegree_gallop", ctypes.c_uint32 * KCL_MAX_CLASSES),
+                ("sdegree_gallop_list", ctypes.c_uint32 * KCL_MAX_CLASSES),
+                ("sdegree_bitmap", ctypes.c_uint32 * KCL_MAX_CLASSES)]
+
+    def as_dict(self):
+        return {f: [int(x) for x in getattr(self, f)] for f, _ in self._fields_}
+
+
 _P, _U32, _U64, _I = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int
 _sig = {
     "kcl_load_csr": ([_U32, _P, _P, _I, _P, ctypes.POINTER(_P)], _I),
@@ -76,6 +85,12 @@ _sig = {
                         ctypes.POINTER(_U32)], _I),
     "kcl_enable_timing": ([_P, _I], _I),
     "kcl_last_timing": ([_P, ctypes.POINTER(_Timing)], _I),
+    "kcl_set_options": ([_P, _U32], _I),
+    "kcl_get_options": ([_P, ctypes.POINTER(_U32)], _I),
+    "kcl_scratch_bytes": ([_P, ctypes.POINTER(_U64), ctypes.POINTER(_U64)], _I),
+    "kcl_get_tuning": ([_P, ctypes.POINTER(_Tuning)], _I),
+    "kcl_set_tuning": ([_P, ctypes.POINTER(_Tuning)], _I),
+    "kcl_autotune": ([_P, _U32, _I, _I, ctypes.POINTER(_Tuning)], _I),
     "kcl_strerror": ([_I], ctypes.c_char_p),
 }
 for _name, (_args, _res) in _sig.items():
@@ -241,6 +256,55 @@ def kcl_stage_info(g, k, ordering):
 
 def kcl_enable_timing(g, enable=True):
     _check(_lib.kcl_enable_timing(g.handle, 1 if enable else 0), "kcl_enable_timing")
+
+
+KCL_OPT_NO_PRECORE = 1
+KCL_OPT_NO_PRELIST = 2
+KCL_OPT_NO_COLOR_PRUNE = 4
+
+
+def kcl_set_options(g, flags):
+    """Ablation switches (KCL_OPT_* bits); results do not change."""
+    _check(_lib.kcl_set_options(g.handle, int(flags)), "kcl_set_options")
+
+
+def kcl_get_options(g):
+    f = ctypes.c_uint32()
+    _check(_lib.kcl_get_options(g.handle, ctypes.byref(f)), "kcl_get_options")
+    return int(f.value)
+
+
+def kcl_scratch_bytes(g):
+    """(workspace, arena) device bytes the handle holds now."""
+    a, b = ctypes.c_uint64(), ctypes.c_uint64()
+    _check(_lib.kcl_scratch_bytes(g.handle, ctypes.byref(a), ctypes.byref(b)), "kcl_scratch_bytes")
+    return int(a.value), int(b.value)
+
+
+def kcl_get_tuning(g):
+    """The graph's listing-kernel tuning as a dict of per-class lists."""
+    t = _Tuning()
+    _check(_lib.kcl_get_tuning(g.handle, ctypes.byref(t)), "kcl_get_tuning")
+    return t.as_dict()
+
+
+def kcl_set_tuning(g, tuning):
+    """Set the tuning from a dict like kcl_get_tuning's (missing classes: 0)."""
+    t = _Tuning()
+    for f, _ in _Tuning._fields_:
+        arr = getattr(t, f)
+        for c, v in enumerate(tuning.get(f, [])[:KCL_MAX_CLASSES]):
+            arr[c] = int(v)
+    _check(_lib.kcl_set_tuning(g.handle, ctypes.byref(t)), "kcl_set_tuning")
+
+
+def kcl_autotune(g, k, ordering, listing=False):
+    """Run the autotuner for (k, ordering) in counting or listing mode on g;
+    returns the chosen tuning."""
+    t = _Tuning()
+    _check(_lib.kcl_autotune(g.handle, k, _ord(ordering), 1 if listing else 0, ctypes.byref(t)),
+           "kcl_autotune")
+    return t.as_dict()
 
 
 def kcl_last_timing(g):

@@ -250,7 +250,8 @@ kcl_status run_front(kcl_graph *g, uint32_t k, kcl_ordering ord, const kcl_ring 
 
     // ---- stage 0: Pre-Core
     T.begin(0);
-    T.add(0, launch_precore_init(g, k, w, s));
+    // without Pre-Core the threshold is 0: every vertex stays
+    T.add(0, launch_precore_init(g, (g->options & KCL_OPT_NO_PRECORE) ? 1u : k, w, s));
     uint32_t *fa = w.frontier_a, *fb = w.frontier_b;
     for (;;) {
         uint32_t nin = 0;
@@ -265,8 +266,8 @@ kcl_status run_front(kcl_graph *g, uint32_t k, kcl_ordering ord, const kcl_ring 
 
     // ---- stage 1: Pre-List
     T.begin(1);
-    T.add(1, launch_prelist(g, k, w, listing ? 1 : 0, s));
-    if (listing) {
+    if (!(g->options & KCL_OPT_NO_PRELIST)) T.add(1, launch_prelist(g, k, w, listing ? 1 : 0, s));
+    if (listing && !(g->options & KCL_OPT_NO_PRELIST)) {
         uint32_t ncomp = 0;
         KCL_TRY(read_u32(g, &w.res->n_clique_comps, &ncomp));
         T.add(1, launch_prelist_emit(g, k, w, ncomp, ring, s));
@@ -748,6 +749,106 @@ kcl_status kcl_last_timing(const kcl_graph *g, kcl_timing *t) {
         t->class_roots[c] = g->timing.class_roots[c];
         t->class_ms[c] = g->timing.class_ms[c];
     }
+    return KCL_OK;
+}
+
+kcl_status kcl_set_options(kcl_graph *g, uint32_t flags) {
+    if (!g || (flags & ~(KCL_OPT_NO_PRECORE | KCL_OPT_NO_PRELIST | KCL_OPT_NO_COLOR_PRUNE)))
+        return KCL_EINVAL;
+    g->options = flags;
+    return KCL_OK;
+}
+
+kcl_status kcl_get_options(const kcl_graph *g, uint32_t *flags) {
+    if (!g || !flags) return KCL_EINVAL;
+    *flags = g->options;
+    return KCL_OK;
+}
+
+kcl_status kcl_scratch_bytes(const kcl_graph *g, uint64_t *workspace, uint64_t *arena) {
+    if (!g || !workspace || !arena) return KCL_EINVAL;
+    const Workspace &w = g->ws;
+    uint64_t ws = 0;
+    if (w.res) {
+        // mirrors ensure_workspace's allocations
+        const uint64_t n = (uint64_t)w.n_cap + 1, half = w.nnz_cap / 2 + 1;
+        ws = 2 * n                                  // alive, alive_core
+             + 4 * n * 13 + 8 * n                   // u32 arrays, comp_sdeg
+             + 4 * 2                                // outdeg, optr extra entry
+             + 4 * half                             // oadj
+             + 4 * (3 * n + 1024) + 4 * (n / 1024 + 1024) + 4 * 64
+             + sizeof(DevResult) + sizeof(PeelCtl);
+    }
+    *workspace = ws;
+    *arena = (uint64_t)w.arena_words * 4;
+    return KCL_OK;
+}
+
+kcl_status kcl_get_tuning(const kcl_graph *g, kcl_tuning *t) {
+    if (!g || !t) return KCL_EINVAL;
+    *t = g->tuning;
+    return KCL_OK;
+}
+
+kcl_status kcl_set_tuning(kcl_graph *g, const kcl_tuning *t) {
+    if (!g || !t) return KCL_EINVAL;
+    g->tuning = *t;
+    return KCL_OK;
+}
+
+namespace {
+
+// One tuning pass: for every candidate value of knob[] (all classes at once)
+// run the call and keep, per class, the fastest value.
+kcl_status tune_knob(kcl_graph *g, uint32_t k, kcl_ordering ord, int listing, uint32_t *knob,
+                     const uint32_t *cand, int ncand) {
+    float best_ms[KCL_MAX_CLASSES];
+    uint32_t best[KCL_MAX_CLASSES];
+    for (int c = 0; c < KCL_MAX_CLASSES; c++) {
+        best_ms[c] = -1.f;
+        best[c] = knob[c];
+    }
+    uint64_t cnt = 0, cks = 0, wr = 0;
+    for (int i = 0; i < ncand; i++) {
+        for (int c = 0; c < KCL_MAX_CLASSES; c++) knob[c] = cand[i];
+        kcl_status st = listing ? kcl_list(g, k, ord, nullptr, &cnt, &cks, &wr) : kcl_count(g, k, ord, &cnt);
+        if (st != KCL_OK) {
+            for (int c = 0; c < KCL_MAX_CLASSES; c++) knob[c] = best[c];
+            return st;
+        }
+        for (uint32_t c = 0; c < g->timing.n_classes && c < KCL_MAX_CLASSES; c++) {
+            if (!g->timing.class_roots[c]) continue;
+            const float ms = g->timing.class_ms[c];
+            if (best_ms[c] < 0.f || ms < 0.98f * best_ms[c]) {
+                best_ms[c] = ms;
+                best[c] = cand[i];
+            }
+        }
+    }
+    for (int c = 0; c < KCL_MAX_CLASSES; c++) knob[c] = best[c];
+    return KCL_OK;
+}
+
+}  // namespace
+
+kcl_status kcl_autotune(kcl_graph *g, uint32_t k, kcl_ordering ord, int listing, kcl_tuning *out) {
+    if (!g) return KCL_EINVAL;
+    KCL_TRY(check_args(g, k, ord));
+    const int was_enabled = g->timing.enabled;
+    KCL_TRY(kcl_enable_timing(g, 1));
+    kcl_status st = KCL_OK;
+    if (ord == KCL_ORDER_DEGREE) {
+        static const uint32_t bitmap_cand[] = {0, 4, 64, 0xFFFFFFFFu};
+        static const uint32_t gallop_cand[] = {0, 40, 80, 160, 400};
+        st = tune_knob(g, k, ord, listing, g->tuning.sdegree_bitmap, bitmap_cand, 4);
+        if (st == KCL_OK)
+            st = tune_knob(g, k, ord, listing,
+                           listing ? g->tuning.sdegree_gallop_list : g->tuning.sdegree_gallop,
+                           gallop_cand, 5);
+    }
+    if (!was_enabled) kcl_enable_timing(g, 0);
+    if (st != KCL_OK) return st;
+    if (out) *out = g->tuning;
     return KCL_OK;
 }
 

@@ -35,14 +35,24 @@ constexpr unsigned kFull = 0xffffffffu;
 // rows, old index) and B (colour-DAG rows, new index) may live in a global
 // arena instead (a_global / b_global), in which case they take no room here.
 struct SubLay {
-    uint32_t W, D, WP, NBR, PRE, IDS, HK, HV, U16, META, PEND, A, B, total;
+    uint32_t W, D, WP, WPB, NBR, PRE, IDS, HK, HV, U16, META, PEND, A, B, total;
 };
+
+// Row strides.  A (build only): odd, so 32 lanes reading 32 rows hit 32
+// banks.  B (read by the DFS): for W >= 4 a multiple of 4 words with an odd
+// number of 16-byte chunks, so rows are read as 128-bit vectors and 8 lanes
+// reading 8 consecutive rows hit 8 different bank quads.
+__host__ __device__ inline uint32_t a_stride(uint32_t W) { return (W & 1) ? W : W + 1; }
+__host__ __device__ inline uint32_t b_stride(uint32_t W) {
+    return W >= 4 ? (((W >> 2) & 1) ? W : W + 4) : a_stride(W);
+}
 
 __host__ __device__ inline SubLay sub_layout(uint32_t W, bool a_global, bool b_global) {
     SubLay L;
     L.W = W;
     L.D = 32 * W;
-    L.WP = (W & 1) ? W : W + 1;
+    L.WP = a_stride(W);
+    L.WPB = b_stride(W);
     L.NBR = 0;
     L.PRE = L.NBR + L.D;        // D + 1
     L.IDS = L.PRE + L.D + 1;    // D
@@ -54,15 +64,18 @@ __host__ __device__ inline SubLay sub_layout(uint32_t W, bool a_global, bool b_g
     uint32_t end = L.PEND + (L.D + 1) / 2;
     L.A = a_global ? 0 : end;
     if (!a_global) end += L.D * L.WP;
+    end = (end + 3) & ~3u;  // B rows start on a 16-byte boundary
     L.B = b_global ? 0 : end;
-    if (!b_global) end += L.D * L.WP;
+    if (!b_global) end += L.D * L.WPB;
     L.total = (end + 3) & ~3u;
     return L;
 }
 
 // Per-warp DFS stack: C and pending-children bitmaps per depth, path, cursor.
+// C and P per depth (2 k W), path and cursor (2 k), sortedR (32), leaf
+// candidate queue (64 u16)
 __host__ __device__ inline uint32_t dfs_words(uint32_t W, uint32_t k) {
-    return (k * (2 * W + 2) + 32 + 3) & ~3u;
+    return (k * (2 * W + 2) + 32 + 32 + 3) & ~3u;
 }
 
 struct Sub {
@@ -103,15 +116,6 @@ struct Grp {
     }
 };
 
-__device__ __forceinline__ uint32_t warp_incl_scan(uint32_t x) {
-    const unsigned lane = lane_id();
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        uint32_t y = __shfl_up_sync(kFull, x, o);
-        if (lane >= (unsigned)o) x += y;
-    }
-    return x;
-}
 
 // --------------------------------------------------------------- build
 // Steps 1-3 above; leaves B', colp, start, ids and meta[0] = ncol.
@@ -120,7 +124,7 @@ __device__ void build_sub(uint32_t d, uint32_t base, uint32_t Wrt, const uint32_
                           const uint32_t *__restrict__ oadj, const Sub &s) {
     using G = Grp<NW>;
     const uint32_t W = WT ? (uint32_t)WT : Wrt;
-    const uint32_t WP = (W & 1) ? W : W + 1;
+    const uint32_t WP = a_stride(W), WPB = b_stride(W);
     const uint32_t tid = G::tid(), lane = lane_id(), warp = G::warp();
 
     // out-list lengths of N+_u (scanned below), row starts, zero rows
@@ -131,10 +135,8 @@ __device__ void build_sub(uint32_t d, uint32_t base, uint32_t Wrt, const uint32_
         s.ids[i] = r0;
         s.pre[i] = optr[v + 1] - r0;
     }
-    for (uint32_t i = tid; i < d * WP; i += G::size()) {
-        s.A[i] = 0;
-        s.B[i] = 0;
-    }
+    for (uint32_t i = tid; i < d * WP; i += G::size()) s.A[i] = 0;
+    for (uint32_t i = tid; i < d * WPB; i += G::size()) s.B[i] = 0;
     G::sync();
     if (warp == 0) {
         uint32_t running = 0;
@@ -225,7 +227,7 @@ __device__ void build_sub(uint32_t d, uint32_t base, uint32_t Wrt, const uint32_
                 bool fits = false;
                 if (c <= ncol) {
                     uint32_t acc = 0;
-                    for (uint32_t w = 0; w < W; w++) acc |= s.A[v * WP + w] & s.B[(c - 1) * WP + w];
+                    for (uint32_t w = 0; w < W; w++) acc |= s.A[v * WP + w] & s.B[(c - 1) * WPB + w];
                     fits = acc == 0;
                 } else if (c == ncol + 1) {
                     fits = true;
@@ -235,7 +237,7 @@ __device__ void build_sub(uint32_t d, uint32_t base, uint32_t Wrt, const uint32_
             }
             if (chosen > ncol) ncol = chosen;
             if (lane == 0) {
-                s.B[(chosen - 1) * WP + (v >> 5)] |= 1u << (v & 31);
+                s.B[(chosen - 1) * WPB + (v >> 5)] |= 1u << (v & 31);
                 s.colour_old[v] = (uint16_t)chosen;
             }
             __syncwarp();
@@ -246,7 +248,7 @@ __device__ void build_sub(uint32_t d, uint32_t base, uint32_t Wrt, const uint32_
             uint32_t c = c0 + lane + 1;
             uint32_t sz = 0;
             if (c <= ncol)
-                for (uint32_t w = 0; w < W; w++) sz += __popc(s.B[(c - 1) * WP + w]);
+                for (uint32_t w = 0; w < W; w++) sz += __popc(s.B[(c - 1) * WPB + w]);
             uint32_t incl = warp_incl_scan(sz);
             if (c <= ncol) s.start[c] = (uint16_t)(run + incl - sz);
             run += __shfl_sync(kFull, incl, 31);
@@ -260,7 +262,7 @@ __device__ void build_sub(uint32_t d, uint32_t base, uint32_t Wrt, const uint32_
     G::sync();
     for (uint32_t i = tid; i < d; i += G::size()) {
         uint32_t c = s.colour_old[i];
-        const uint32_t *cls = s.B + (c - 1) * WP;
+        const uint32_t *cls = s.B + (c - 1) * WPB;
         uint32_t r = 0;
         for (uint32_t w = 0; w < (i >> 5); w++) r += __popc(cls[w]);
         r += __popc(cls[i >> 5] & ((1u << (i & 31)) - 1u));
@@ -270,14 +272,14 @@ __device__ void build_sub(uint32_t d, uint32_t base, uint32_t Wrt, const uint32_
         s.ids[p] = s.nbr[i];
     }
     G::sync();
-    for (uint32_t i = tid; i < d * WP; i += G::size()) s.B[i] = 0;
+    for (uint32_t i = tid; i < d * WPB; i += G::size()) s.B[i] = 0;
     G::sync();
     // B'(p): out-neighbours (lower colour = index below start[colour]); one
     // thread per row, so no two threads write the same row
     for (uint32_t i = tid; i < d; i += G::size()) {
         uint32_t p = s.old2new[i];
         uint32_t lim = s.start[s.colour_old[i]];
-        uint32_t *row = s.B + p * WP;
+        uint32_t *row = s.B + p * WPB;
         for (uint32_t w = 0; w < W; w++) {
             uint32_t m = s.A[i * WP + w];
             while (m) {
@@ -298,6 +300,7 @@ struct Emit {
     int wrap;
     unsigned long long *root_cks;  // listing: per-root checksum sums, or null
     const uint32_t *idmap;         // listing: vertex -> output id, or null (identity)
+    uint32_t prune;                // 1: Lemma 1 colour prune (0 only for ablations)
 };
 
 struct View {  // read-only view of a built subproblem, per warp
@@ -305,9 +308,13 @@ struct View {  // read-only view of a built subproblem, per warp
     const uint16_t *colp, *start;
     const uint32_t *ids;
     uint32_t d, W, WP, ncol, u, k;
+    uint32_t prune;  // 0: expand every candidate (ablation of Lemma 1)
 };
 
+// First candidate index at level l: the vertices of colour >= l (Lemma 1),
+// which the colour-sorted indexing makes a suffix.
 __device__ __forceinline__ uint32_t start_of(const View &v, uint32_t l) {
+    if (!v.prune) return 0;
     return l <= v.ncol + 1 ? (uint32_t)v.start[l] : v.d;
 }
 
@@ -320,19 +327,115 @@ __device__ __forceinline__ uint32_t cand_word(const uint32_t *C, uint32_t j, uin
     return m;
 }
 
+// |row & C| over the first wl words.  For W >= 4 both are read as 128-bit
+// vectors up to round4(wl) <= W: C is zero beyond its cw words and a row is
+// zero beyond ceil(start[colour] / 32) words, so the extra words add nothing.
+__device__ __forceinline__ uint32_t and_popc(const uint32_t *row, const uint32_t *C, uint32_t wl,
+                                             uint32_t W) {
+    uint32_t x = 0;
+    if (W >= 4) {
+        const uint4 *r4 = reinterpret_cast<const uint4 *>(row);
+        const uint4 *c4 = reinterpret_cast<const uint4 *>(C);
+        for (uint32_t t = 0; t < (wl + 3) >> 2; t++) {
+            const uint4 a = r4[t], b = c4[t];
+            x += __popc(a.x & b.x) + __popc(a.y & b.y) + __popc(a.z & b.z) + __popc(a.w & b.w);
+        }
+    } else {
+        for (uint32_t t = 0; t < wl; t++) x += __popc(row[t] & C[t]);
+    }
+    return x;
+}
+
 __device__ __forceinline__ uint32_t row_words(const View &v, uint32_t p, uint32_t cw) {
     uint32_t wl = (v.start[v.colp[p]] + 31) >> 5;
     return wl < cw ? wl : cw;
 }
 
+// A batch of nb <= 32 leaf candidates q[0..nb): lane i takes candidate q[i]
+// and closes |B'(q[i]) & C| cliques.
+template <bool LIST>
+__device__ void leaf_batch(const View &v, const uint32_t *C, uint32_t cw, const uint16_t *q,
+                           uint32_t nb, const uint32_t *sortedR, const Emit &em, DevResult *res,
+                           unsigned long long &cnt, unsigned long long &cks) {
+    const unsigned lane = lane_id();
+    uint32_t x = 0;
+    if (lane < nb) {
+        const uint32_t p = q[lane];
+        const uint32_t *row = v.B + p * v.WP;
+        x = and_popc(row, C, row_words(v, p, cw), v.W);
+    }
+    cnt += x;
+    if (!LIST) return;
+    // the tot cliques of the batch are enumerated by all lanes together:
+    // clique r belongs to the lane o whose exclusive prefix holds it, and is
+    // the (r - excl_o)-th set bit of B'(q[o]) & C -- hashing is spread evenly
+    const uint32_t incl = warp_incl_scan(x);
+    const uint32_t excl = incl - x;
+    const uint32_t tot = __shfl_sync(kFull, incl, 31);
+    unsigned long long slot0 = 0;
+    if (tot && em.ring) {
+        if (lane == 0) slot0 = atomicAdd(&res->emitted, (unsigned long long)tot);
+        slot0 = __shfl_sync(kFull, slot0, 0);
+    }
+    for (uint32_t base = 0; base < tot; base += 32) {
+        const uint32_t r = base + lane;
+        uint32_t o = 0;  // number of lanes whose inclusive prefix is <= r
+#pragma unroll
+        for (uint32_t step = 16; step > 0; step >>= 1) {
+            const uint32_t vv = __shfl_sync(kFull, incl, o + step - 1);
+            if (vv <= r) o += step;
+        }
+        const uint32_t eo = __shfl_sync(kFull, excl, o & 31u);
+        if (r >= tot) continue;
+        const uint32_t po = q[o];
+        const uint32_t *row = v.B + po * v.WP;
+        const uint32_t wl = row_words(v, po, cw);
+        uint32_t rank = r - eo, qq = 0;
+        for (uint32_t t = 0; t < wl; t++) {
+            const uint32_t mm = row[t] & C[t];
+            const uint32_t c = __popc(mm);
+            if (rank < c) {
+                qq = t * 32 + __fns(mm, 0, (int)rank + 1);
+                break;
+            }
+            rank -= c;
+        }
+        const uint32_t a = v.ids[po], b = v.ids[qq];
+        const uint32_t k = v.k;
+        uint32_t ex[2] = {a < b ? a : b, a < b ? b : a};
+        uint32_t rec[KCL_MAX_K];
+        uint32_t nr = k - 2, ri = 0, ei = 0, oo = 0;
+        while (ri < nr || ei < 2) {
+            uint32_t rr = ri < nr ? sortedR[ri] : 0xFFFFFFFFu;
+            if (ei < 2 && ex[ei] < rr) rec[oo++] = ex[ei++];
+            else rec[oo++] = sortedR[ri++];
+        }
+        uint64_t h = hash_seed(k);
+        for (uint32_t z = 0; z < k; z++) h = mix64(h ^ (uint64_t)rec[z]);
+        cks += h;
+        if (em.ring) {
+            unsigned long long sl = slot0 + r;
+            bool ok = true;
+            if (em.wrap) sl %= em.capacity;
+            else ok = sl < em.capacity;
+            if (ok)
+                for (uint32_t z = 0; z < k; z++) em.ring[sl * k + z] = rec[z];
+        }
+    }
+}
+
 // Leaf (l = 2) over candidate words j0, j0+js, ... < cw: each candidate p
-// closes |B'(p) & C| cliques.  depth = number of path entries below the root.
+// (colour >= 2) closes |B'(p) & C| cliques.  The candidates of consecutive
+// words are packed into a per-warp queue (64 entries after sortedR) and
+// evaluated 32 at a time, so lanes stay busy when the words are sparse.
+// depth = number of path entries below the root.
 template <bool LIST>
 __device__ void leaf(const View &v, const uint32_t *C, uint32_t cw, uint32_t depth, uint32_t j0,
                      uint32_t js, const uint32_t *path, uint32_t *sortedR, const Emit &em,
                      DevResult *res, unsigned long long &cnt, unsigned long long &cks) {
     const unsigned lane = lane_id();
     const uint32_t s = start_of(v, 2);
+    uint16_t *q = reinterpret_cast<uint16_t *>(sortedR + 32);
     if (LIST) {
         if (lane == 0) {
             sortedR[0] = v.u;
@@ -344,62 +447,25 @@ __device__ void leaf(const View &v, const uint32_t *C, uint32_t cw, uint32_t dep
         }
         __syncwarp();
     }
+    uint32_t pend = 0;  // queued candidates (< 32 between words)
     for (uint32_t j = j0; j < cw; j += js) {
-        uint32_t m = cand_word(C, j, s);
+        const uint32_t m = cand_word(C, j, s);
         if (!m) continue;
-        const uint32_t p = j * 32 + lane;
-        const bool mine = (m >> lane) & 1u;
-        uint32_t x = 0;
-        if (mine) {
-            const uint32_t *row = v.B + p * v.WP;
-            uint32_t wl = row_words(v, p, cw);
-            for (uint32_t t = 0; t < wl; t++) x += __popc(row[t] & C[t]);
+        if ((m >> lane) & 1u) q[pend + __popc(m & ((1u << lane) - 1u))] = (uint16_t)(j * 32 + lane);
+        pend += __popc(m);
+        if (pend >= 32) {
+            __syncwarp();
+            leaf_batch<LIST>(v, C, cw, q, 32, sortedR, em, res, cnt, cks);
+            __syncwarp();
+            if (lane < pend - 32) q[lane] = q[32 + lane];
+            pend -= 32;
+            __syncwarp();
         }
-        cnt += x;
-        if (LIST) {
-            uint32_t incl = warp_incl_scan(x);
-            uint32_t tot = __shfl_sync(kFull, incl, 31);
-            unsigned long long slot0 = 0;
-            if (tot && em.ring) {
-                if (lane == 0) slot0 = atomicAdd(&res->emitted, (unsigned long long)tot);
-                slot0 = __shfl_sync(kFull, slot0, 0);
-            }
-            if (mine && x) {
-                unsigned long long slot = slot0 + (incl - x);
-                const uint32_t *row = v.B + p * v.WP;
-                const uint32_t a = v.ids[p];
-                const uint32_t wl = row_words(v, p, cw);
-                const uint32_t k = v.k;
-                for (uint32_t t = 0; t < wl; t++) {
-                    uint32_t mm = row[t] & C[t];
-                    while (mm) {
-                        uint32_t q = t * 32 + (__ffs(mm) - 1);
-                        mm &= mm - 1;
-                        uint32_t b = v.ids[q];
-                        uint32_t ex[2] = {a < b ? a : b, a < b ? b : a};
-                        uint32_t rec[KCL_MAX_K];
-                        uint32_t nr = k - 2, ri = 0, ei = 0, o = 0;
-                        while (ri < nr || ei < 2) {
-                            uint32_t r = ri < nr ? sortedR[ri] : 0xFFFFFFFFu;
-                            if (ei < 2 && ex[ei] < r) rec[o++] = ex[ei++];
-                            else rec[o++] = sortedR[ri++];
-                        }
-                        uint64_t h = hash_seed(k);
-                        for (uint32_t z = 0; z < k; z++) h = mix64(h ^ (uint64_t)rec[z]);
-                        cks += h;
-                        if (em.ring) {
-                            unsigned long long sl = slot;
-                            bool ok = true;
-                            if (em.wrap) sl %= em.capacity;
-                            else ok = sl < em.capacity;
-                            if (ok)
-                                for (uint32_t z = 0; z < k; z++) em.ring[sl * k + z] = rec[z];
-                        }
-                        slot++;
-                    }
-                }
-            }
-        }
+    }
+    if (pend) {
+        __syncwarp();
+        leaf_batch<LIST>(v, C, cw, q, pend, sortedR, em, res, cnt, cks);
+        __syncwarp();
     }
 }
 
@@ -414,9 +480,7 @@ __device__ void expand(const View &v, const uint32_t *C, uint32_t cw, uint32_t l
         if ((m >> lane) & 1u) {
             uint32_t p = j * 32 + lane;
             const uint32_t *row = v.B + p * v.WP;
-            uint32_t wl = row_words(v, p, cw);
-            uint32_t x = 0;
-            for (uint32_t t = 0; t < wl; t++) x += __popc(row[t] & C[t]);
+            const uint32_t x = and_popc(row, C, row_words(v, p, cw), v.W);
             ok = x + 1 >= l;
         }
         unsigned bal = __ballot_sync(kFull, ok);
@@ -547,7 +611,7 @@ __global__ void __launch_bounds__(128) k_bitcol_warp(uint32_t k, const uint32_t 
             __syncwarp();
         }
         const uint32_t uo = (LIST && em.idmap) ? em.idmap[u] : u;
-        View v{s.B, s.colp, s.start, s.ids, d, WT, L.WP, s.meta[0], uo, k};
+        View v{s.B, s.colp, s.start, s.ids, d, WT, L.WPB, s.meta[0], uo, k, em.prune};
         if (k == 3) {
             const uint32_t dw = (d + 31) >> 5;
             for (uint32_t t = lane; t < WT; t += 32)
@@ -597,10 +661,10 @@ __global__ void __launch_bounds__(NW * 32) k_bitcol_cta(uint32_t k, uint32_t W,
     const unsigned lane = lane_id();
     const uint32_t warp = threadIdx.x >> 5;
     const SubLay L = sub_layout(W, AG, BG);
-    const size_t rows = (size_t)L.D * L.WP;
-    uint32_t *slice = arena + (size_t)blockIdx.x * ((AG ? rows : 0) + (BG ? rows : 0));
+    const size_t rows_a = (size_t)L.D * L.WP, rows_b = (size_t)L.D * L.WPB;
+    uint32_t *slice = arena + (size_t)blockIdx.x * ((AG ? rows_a : 0) + (BG ? rows_b : 0));
     uint32_t *Ag = AG ? slice : nullptr;
-    uint32_t *Bg = BG ? slice + (AG ? rows : 0) : nullptr;
+    uint32_t *Bg = BG ? slice + (AG ? rows_a : 0) : nullptr;
     const Sub s = sub_ptrs(smem, L, Ag, Bg);
     uint32_t *stack = smem + L.total + warp * dfs_words(W, k);
     unsigned long long cnt = 0, cks = 0;
@@ -620,7 +684,7 @@ __global__ void __launch_bounds__(NW * 32) k_bitcol_cta(uint32_t k, uint32_t W,
             __syncthreads();
         }
         const uint32_t uo = (LIST && em.idmap) ? em.idmap[u] : u;
-        View v{s.B, s.colp, s.start, s.ids, d, W, L.WP, s.meta[0], uo, k};
+        View v{s.B, s.colp, s.start, s.ids, d, W, L.WPB, s.meta[0], uo, k, em.prune};
         if (k == 3) {
             const uint32_t dw = (d + 31) >> 5;
             for (uint32_t t = lane; t < W; t += 32)
@@ -696,8 +760,8 @@ size_t class_smem(int c, uint32_t k) {
 
 size_t class_arena_per_cta(int c) {
     const ClassCfg &cc = kClass[c];
-    size_t rows = (size_t)32 * cc.W * ((cc.W & 1) ? cc.W : cc.W + 1);
-    return (cc.ag ? rows : 0) + (cc.bg ? rows : 0);
+    const size_t rows_a = (size_t)32 * cc.W * a_stride(cc.W), rows_b = (size_t)32 * cc.W * b_stride(cc.W);
+    return (cc.ag ? rows_a : 0) + (cc.bg ? rows_b : 0);
 }
 
 template <int WT, bool LIST>
@@ -754,7 +818,8 @@ size_t bitcol_arena_words(uint32_t k, int num_sms, uint32_t max_outdeg) {
 int launch_bitcol(const kcl_graph *g, uint32_t k, Workspace &w, const uint32_t *class_begin,
                   int n_classes, const ListArgs &la, cudaStream_t s) {
     // class c covers root positions [class_begin[c], c ? class_begin[c-1] : n_roots)
-    Emit em{la.ring, la.capacity, la.wrap, la.per_root_cks, la.idmap};
+    Emit em{la.ring, la.capacity, la.wrap, la.per_root_cks, la.idmap,
+            (g->options & KCL_OPT_NO_COLOR_PRUNE) ? 0u : 1u};
     int launches = 0;
     cudaMemsetAsync(w.queue, 0, 64 * sizeof(unsigned), s);
     for (int c = 0; c < n_classes; c++) {

@@ -116,6 +116,8 @@ struct kcl_graph {
     bool owns_csr = true;      // false for a view that shares another graph's CSR
     kcl::Workspace ws;
     kcl::Timing timing;
+    kcl_tuning tuning = {};  // listing-kernel knobs (results never depend on them)
+    uint32_t options = 0;    // KCL_OPT_* ablation switches
 };
 
 namespace kcl {
@@ -133,6 +135,17 @@ __device__ __forceinline__ uint64_t hash_seed(uint32_t k) {
 }
 
 __device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
+
+// Inclusive prefix sum over the 32 lanes of a warp (all lanes active).
+__device__ __forceinline__ uint32_t warp_incl_scan(uint32_t x) {
+    const unsigned lane = lane_id();
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= (unsigned)o) x += y;
+    }
+    return x;
+}
 
 // Add to a 64-bit counter and flag a wrap-around in `carry`.
 __device__ __forceinline__ void add_count(unsigned long long *dst, unsigned long long *carry,

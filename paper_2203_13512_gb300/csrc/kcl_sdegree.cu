@@ -224,19 +224,22 @@ constexpr uint16_t kPad = 0xFFFF;  // above every local index (< 1024)
 
 __host__ __device__ inline uint32_t round4(uint32_t x) { return (x + 3) & ~3u; }
 
-__host__ __device__ inline uint32_t stack_words(uint32_t cap, uint32_t k) {
+// Listing: (candidate, match) pairs waiting to be hashed, per warp.
+constexpr uint32_t kEmitBuf = 256;
+
+__host__ __device__ inline uint32_t stack_words(uint32_t cap, uint32_t k, bool list) {
     // clist and pend: (k-2) lists of round4(cap) u16 each; csize, npend,
-    // ppos, path: k words each; sortedR: 32 words
-    return (2 * ((k - 2) * round4(cap) / 2) + 4 * k + 32 + 3) & ~3u;
+    // ppos, path: k words each; sortedR: 32 words; listing: the pair buffer
+    return (2 * ((k - 2) * round4(cap) / 2) + 4 * k + 32 + (list ? kEmitBuf : 0u) + 3) & ~3u;
 }
 
 // Warp-per-root layout (words): build scratch, directed bit-rows, lists, one
 // DFS stack with list capacity D.
 struct LLay {
-    uint32_t D, WPD, NBR, LOFS, PRE, RS, HK, HV, LEN, BITS, LADJ, STACK, total;
+    uint32_t D, WPD, NBR, LOFS, PRE, RS, HK, HV, LEN, RK, BITS, LADJ, STACK, total;
 };
 
-__host__ __device__ inline LLay make_llayout(uint32_t D, uint32_t k) {
+__host__ __device__ inline LLay make_llayout(uint32_t D, uint32_t k, bool list) {
     LLay L;
     L.D = D;
     uint32_t w = D / 32;
@@ -249,11 +252,29 @@ __host__ __device__ inline LLay make_llayout(uint32_t D, uint32_t k) {
     L.HK = L.RS + D;          // hash keys (2D)
     L.HV = L.HK + 2 * D;      // hash values, u16 (2D)
     L.LEN = L.HV + D;         // list lengths, u16 (D)
-    L.BITS = L.LEN + D / 2;   // directed bit-rows (D x WPD)
+    L.RK = L.LEN + D / 2;     // DAG rank of each member, u16 (D)
+    L.BITS = L.RK + D / 2;    // directed bit-rows (D x WPD)
     L.LADJ = (L.BITS + D * L.WPD + 3) & ~3u;
     L.STACK = (L.LADJ + (uint32_t)((emax + 1) / 2) + 3) & ~3u;
-    L.total = (L.STACK + stack_words(D, k) + 3) & ~3u;
+    L.total = (L.STACK + stack_words(D, k, list) + 3) & ~3u;
     return L;
+}
+
+// One block step of a merge join of padded u16 lists: all 16 pairs of the
+// 4-entry blocks x (from a) and y (from b) compared.  Entries are distinct
+// within a list, so each a_t meets at most one b entry; a padding entry never
+// counts (it may meet padding in b).  Returns the matches; *adv_a / *adv_b
+// say which block to advance (the one with the smaller last entry, or both).
+__device__ __forceinline__ uint32_t block_step4(uint2 x, uint2 y, bool *adv_a, bool *adv_b) {
+    const uint32_t a0 = x.x & 0xFFFFu, a1 = x.x >> 16, a2 = x.y & 0xFFFFu, a3 = x.y >> 16;
+    const uint32_t b0 = y.x & 0xFFFFu, b1 = y.x >> 16, b2 = y.y & 0xFFFFu, b3 = y.y >> 16;
+    uint32_t c = (a0 != kPad) & ((a0 == b0) | (a0 == b1) | (a0 == b2) | (a0 == b3));
+    c += (a1 != kPad) & ((a1 == b0) | (a1 == b1) | (a1 == b2) | (a1 == b3));
+    c += (a2 != kPad) & ((a2 == b0) | (a2 == b1) | (a2 == b2) | (a2 == b3));
+    c += (a3 != kPad) & ((a3 == b0) | (a3 == b1) | (a3 == b2) | (a3 == b3));
+    *adv_a = a3 <= b3;
+    *adv_b = b3 <= a3;
+    return c;
 }
 
 // |a intersect b| for padded u16 lists (8-byte aligned, lengths na, nb),
@@ -266,17 +287,10 @@ __device__ __forceinline__ uint32_t merge_count4(const uint16_t *a, uint32_t na,
     const uint32_t na4 = (na + 3) >> 2, nb4 = (nb + 3) >> 2;
     uint32_t i = 0, j = 0, c = 0;
     while (i < na4 && j < nb4 && c < stop) {
-        const uint2 x = A[i], y = B[j];
-        const uint32_t a0 = x.x & 0xFFFFu, a1 = x.x >> 16, a2 = x.y & 0xFFFFu, a3 = x.y >> 16;
-        const uint32_t b0 = y.x & 0xFFFFu, b1 = y.x >> 16, b2 = y.y & 0xFFFFu, b3 = y.y >> 16;
-        // entries are distinct within a list, so each a_t meets at most one
-        // b entry; a padding entry never counts (it may meet padding in b)
-        c += (a0 != kPad) & ((a0 == b0) | (a0 == b1) | (a0 == b2) | (a0 == b3));
-        c += (a1 != kPad) & ((a1 == b0) | (a1 == b1) | (a1 == b2) | (a1 == b3));
-        c += (a2 != kPad) & ((a2 == b0) | (a2 == b1) | (a2 == b2) | (a2 == b3));
-        c += (a3 != kPad) & ((a3 == b0) | (a3 == b1) | (a3 == b2) | (a3 == b3));
-        i += a3 <= b3;
-        j += b3 <= a3;
+        bool ai, bj;
+        c += block_step4(A[i], B[j], &ai, &bj);
+        i += ai;
+        j += bj;
     }
     return c;
 }
@@ -326,6 +340,7 @@ struct LView {
     const uint16_t *len;   // list lengths
     const uint16_t *ladj;  // reduced out-lists, ascending local indices, padded
     uint32_t d, u, k;
+    uint32_t gallop;       // leaf form threshold (kcl_tuning.sdegree_gallop); 0 = merges
     __device__ __forceinline__ uint32_t deg(uint32_t i) const { return len[i]; }
     __device__ __forceinline__ const uint16_t *list(uint32_t i) const { return ladj + lofs[i]; }
 };
@@ -333,10 +348,11 @@ struct LView {
 struct LStack {
     uint16_t *clist, *pend;  // (k-2) lists of cap entries each
     uint32_t *csize, *npend, *ppos, *path, *sortedR;
+    uint32_t *ebuf;          // listing: kEmitBuf (candidate << 16 | match) pairs
     uint32_t cap;            // a multiple of 4
 };
 
-__device__ inline LStack stack_ptrs(uint32_t *S, uint32_t cap, uint32_t k) {
+__device__ inline LStack stack_ptrs(uint32_t *S, uint32_t cap, uint32_t k, bool list) {
     LStack st;
     st.cap = round4(cap);
     uint32_t lw = (k - 2) * st.cap / 2;
@@ -347,16 +363,75 @@ __device__ inline LStack stack_ptrs(uint32_t *S, uint32_t cap, uint32_t k) {
     st.ppos = st.npend + k;
     st.path = st.ppos + k;
     st.sortedR = st.path + k;
+    st.ebuf = list ? st.sortedR + 32 : nullptr;
     return st;
 }
 
+// Lower-bound search of x in the sorted list a[0..n) by power-of-two steps
+// (the same number of steps for every x, so lanes searching one list stay
+// converged); true when x is present.
+__device__ __forceinline__ bool search16(const uint16_t *a, uint32_t n, uint32_t x) {
+    uint32_t lo = 0;
+    for (uint32_t step = n ? 1u << (31 - __clz(n)) : 0u; step; step >>= 1)
+        if (lo + step <= n && a[lo + step - 1] < x) lo += step;
+    return lo < n && a[lo] == x;
+}
+
+// Listing: hash the nb (candidate << 16 | match) pairs of st.ebuf with all
+// lanes; each pair closes the clique R + {candidate, match}.
+__device__ void flush_pairs(const LView &v, uint32_t nb, const LStack &st, const Emit &em,
+                            DevResult *res, unsigned long long &cks) {
+    const unsigned lane = lane_id();
+    const uint32_t k = v.k;
+    __syncwarp();
+    unsigned long long slot0 = 0;
+    if (em.ring) {
+        if (lane == 0) slot0 = atomicAdd(&res->emitted, (unsigned long long)nb);
+        slot0 = __shfl_sync(kFull, slot0, 0);
+    }
+    for (uint32_t e = lane; e < nb; e += 32) {
+        const uint32_t pr = st.ebuf[e];
+        const uint32_t va = v.nbr[pr >> 16], vb = v.nbr[pr & 0xFFFFu];
+        uint32_t ex[2] = {va < vb ? va : vb, va < vb ? vb : va};
+        uint32_t rec[KCL_MAX_K];
+        uint32_t nr = k - 2, ri = 0, ei = 0, o = 0;
+        while (ri < nr || ei < 2) {
+            uint32_t r = ri < nr ? st.sortedR[ri] : 0xFFFFFFFFu;
+            if (ei < 2 && ex[ei] < r) rec[o++] = ex[ei++];
+            else rec[o++] = st.sortedR[ri++];
+        }
+        uint64_t h = hash_seed(k);
+        for (uint32_t z = 0; z < k; z++) h = mix64(h ^ (uint64_t)rec[z]);
+        cks += h;
+        if (em.ring) {
+            unsigned long long sl = slot0 + e;
+            bool ok = true;
+            if (em.wrap) sl %= em.capacity;
+            else ok = sl < em.capacity;
+            if (ok)
+                for (uint32_t z = 0; z < k; z++) em.ring[sl * k + z] = rec[z];
+        }
+    }
+    __syncwarp();
+}
+
 // Leaf (l = 2): every candidate w = C[i], i in [b0, b1), closes
-// |L(w) intersect C| cliques.  depth = number of path entries below the root.
+// |L(w) intersect C| cliques.  Local indices follow the DAG order, so L(w)
+// holds only indices above w and only C[i+1..] can meet it.  Two forms of
+// the intersections, chosen per leaf by their estimated cost:
+//   galloping: the pairs (i, t), t > i, are spread over the lanes 32 at a
+//     time and lane (i, t) searches C[t] in L(C[i]) -- every lane busy,
+//     |C|^2/2 searches of log |L| steps;
+//   merging: lane i merges L(C[i]) with C[i+1..] in 4 x 4 blocks -- sum of
+//     (|L| + |C|)/4 steps per lane, lanes of unequal length.
+// depth = number of path entries below the root.
 template <bool LIST>
 __device__ void lleaf(const LView &v, const uint16_t *C, uint32_t nC, uint32_t b0, uint32_t b1,
                       uint32_t depth, const LStack &st, const Emit &em, DevResult *res,
                       unsigned long long &cnt, unsigned long long &cks) {
     const unsigned lane = lane_id();
+    const uint32_t jend = b1 < nC ? b1 : (nC ? nC - 1 : 0);  // rows with a non-empty suffix
+    if (b0 >= jend) return;
     if (LIST) {
         if (lane == 0) {
             st.sortedR[0] = v.u;
@@ -368,82 +443,101 @@ __device__ void lleaf(const LView &v, const uint16_t *C, uint32_t nC, uint32_t b
         }
         __syncwarp();
     }
-    for (uint32_t s = b0; s < b1; s += 32) {
-        uint32_t i = s + lane;
+    // cost estimate: merge ~ (sum |L| + pairs) element steps, galloping
+    // ~ pairs searches of lg steps; the tuned threshold weighs the two
+    bool gallop = false;
+    if (v.gallop) {
+        uint32_t lsum = 0;
+        for (uint32_t i = b0 + lane; i < jend; i += 32) lsum += v.deg(C[i]);
+        lsum = __reduce_add_sync(kFull, lsum);
+        const uint64_t rows = jend - b0;
+        const uint64_t pairs = rows * (2ull * nC - b0 - jend - 1) / 2;
+        const uint32_t lg = 32 - __clz((lsum / (uint32_t)rows) | 1u);
+        gallop = pairs * (6ull * lg + 10) * 10 < (lsum + pairs) * (uint64_t)v.gallop;
+    }
+    if (gallop) {
+        uint32_t j = b0, t = b0 + 1 + lane;
+        while (j < jend && t >= nC) { t = t - nC + j + 2; j++; }
+        uint32_t nbuf = 0;
+        for (;;) {
+            const bool valid = j < jend;
+            if (!__any_sync(kFull, valid)) break;
+            bool found = false;
+            uint32_t w = 0, x = 0;
+            if (valid) {
+                w = C[j];
+                x = C[t];
+                found = search16(v.list(w), v.deg(w), x);
+            }
+            cnt += found;
+            if (LIST) {
+                const unsigned m = __ballot_sync(kFull, found);
+                if (found) st.ebuf[nbuf + __popc(m & ((1u << lane) - 1u))] = (w << 16) | x;
+                nbuf += __popc(m);
+                if (nbuf > kEmitBuf - 32) {
+                    flush_pairs(v, nbuf, st, em, res, cks);
+                    nbuf = 0;
+                }
+            }
+            t += 32;
+            while (j < jend && t >= nC) { t = t - nC + j + 2; j++; }
+        }
+        if (LIST && nbuf) flush_pairs(v, nbuf, st, em, res, cks);
+        return;
+    }
+    for (uint32_t s = b0; s < jend; s += 32) {
+        const uint32_t i = s + lane;
         uint32_t x = 0, w = 0;
-        if (i < b1) {
+        if (i < jend) {
             w = C[i];
-            uint32_t dw = v.deg(w);
-            if (dw) x = merge_count4(v.list(w), dw, C, nC, 0xFFFFFFFFu);
+            const uint32_t dw = v.deg(w);
+            const uint32_t q = (i + 1) & ~3u;
+            if (dw) x = merge_count4(v.list(w), dw, C + q, nC - q, 0xFFFFFFFFu);
         }
         cnt += x;
         if (LIST) {
-            uint32_t incl = x;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                uint32_t y = __shfl_up_sync(kFull, incl, o);
-                if (lane >= (unsigned)o) incl += y;
-            }
-            uint32_t tot = __shfl_sync(kFull, incl, 31);
-            unsigned long long slot0 = 0;
-            if (tot && em.ring) {
-                if (lane == 0) slot0 = atomicAdd(&res->emitted, (unsigned long long)tot);
-                slot0 = __shfl_sync(kFull, slot0, 0);
-            }
-            if (x) {
-                unsigned long long slot = slot0 + (incl - x);
-                const uint16_t *a = v.list(w);
-                uint32_t na = v.deg(w), ia = 0, ib = 0;
-                uint32_t vid = v.nbr[w];
-                const uint32_t k = v.k;
-                while (ia < na && ib < nC) {
-                    uint32_t p = a[ia], q = C[ib];
-                    if (p == q) {
-                        uint32_t b2 = v.nbr[p];
-                        uint32_t ex[2] = {vid < b2 ? vid : b2, vid < b2 ? b2 : vid};
-                        uint32_t rec[KCL_MAX_K];
-                        uint32_t nr = k - 2, ri = 0, ei = 0, o = 0;
-                        while (ri < nr || ei < 2) {
-                            uint32_t r = ri < nr ? st.sortedR[ri] : 0xFFFFFFFFu;
-                            if (ei < 2 && ex[ei] < r) rec[o++] = ex[ei++];
-                            else rec[o++] = st.sortedR[ri++];
-                        }
-                        uint64_t h = hash_seed(k);
-                        for (uint32_t z = 0; z < k; z++) h = mix64(h ^ (uint64_t)rec[z]);
-                        cks += h;
-                        if (em.ring) {
-                            unsigned long long sl = slot;
-                            bool ok = true;
-                            if (em.wrap) sl %= em.capacity;
-                            else ok = sl < em.capacity;
-                            if (ok)
-                                for (uint32_t z = 0; z < k; z++) em.ring[sl * k + z] = rec[z];
-                        }
-                        slot++;
-                    }
+            // rounds of kEmitBuf cliques: every lane resumes its merge and
+            // writes its next matches as (candidate, match) pairs at its
+            // prefix position in the round's window; all lanes then hash them
+            const uint32_t incl = warp_incl_scan(x);
+            const uint32_t excl = incl - x;
+            const uint32_t tot = __shfl_sync(kFull, incl, 31);
+            const uint16_t *a = v.list(w);
+            uint32_t ia = 0, ib = i + 1, m = 0;
+            for (uint32_t base = 0; base < tot; base += kEmitBuf) {
+                const uint32_t lim = base + kEmitBuf;
+                while (m < x && excl + m < lim) {
+                    const uint32_t p = a[ia], q = C[ib];
+                    if (p == q) st.ebuf[excl + m - base] = (w << 16) | p, m++;
                     ia += p <= q;
                     ib += q <= p;
                 }
+                const uint32_t nb = tot - base < kEmitBuf ? tot - base : kEmitBuf;
+                flush_pairs(v, nb, st, em, res, cks);
             }
         }
     }
 }
 
-// Inner node at level l: pending children w in C with |L(w) intersect C| >= l-1.
+// Inner node at level l: the positions i of the pending children w = C[i],
+// those with |L(w) intersect C[i+1..]| >= l-1 (a child needs l-1 more
+// vertices, all after it in the DAG order, so the last l-1 entries of C never
+// qualify).
 __device__ uint32_t lexpand(const LView &v, const uint16_t *C, uint32_t nC, uint32_t l, uint16_t *P) {
     const unsigned lane = lane_id();
     uint32_t np = 0;
-    for (uint32_t s = 0; s < nC; s += 32) {
+    const uint32_t lim = nC + 1 >= l ? nC + 1 - l : 0;  // positions i with nC - i - 1 >= l - 1
+    for (uint32_t s = 0; s < lim; s += 32) {
         uint32_t i = s + lane;
         bool ok = false;
-        uint32_t w = 0;
-        if (i < nC) {
-            w = C[i];
-            uint32_t dw = v.deg(w);
-            ok = dw + 1 >= l && merge_count4(v.list(w), dw, C, nC, l - 1) + 1 >= l;
+        if (i < lim) {
+            const uint32_t w = C[i];
+            const uint32_t dw = v.deg(w);
+            const uint32_t q = (i + 1) & ~3u;
+            ok = dw + 1 >= l && merge_count4(v.list(w), dw, C + q, nC - q, l - 1) + 1 >= l;
         }
         unsigned m = __ballot_sync(kFull, ok);
-        if (ok) P[np + __popc(m & ((1u << lane) - 1u))] = (uint16_t)w;
+        if (ok) P[np + __popc(m & ((1u << lane) - 1u))] = (uint16_t)i;
         np += __popc(m);
     }
     return np;
@@ -471,12 +565,14 @@ __device__ void ldfs_child(const LView &v, uint32_t p0, const LStack &st, const 
     while (depth >= 1) {
         const uint32_t pp = st.ppos[depth];
         if (pp >= st.npend[depth]) { depth--; continue; }
-        const uint32_t w = st.pend[(depth - 1) * cap + pp];
+        const uint32_t pos = st.pend[(depth - 1) * cap + pp];
+        const uint16_t *C = depth == 1 ? C1 : st.clist + (depth - 2) * cap;
+        const uint32_t w = C[pos];
         __syncwarp();
         if (lane == 0) { st.ppos[depth] = pp + 1; st.path[depth + 1] = w; }
-        const uint16_t *C = depth == 1 ? C1 : st.clist + (depth - 2) * cap;
         uint16_t *Cn = st.clist + (depth - 1) * cap;  // list of depth + 1
-        const uint32_t nn = warp_intersect16(v.list(w), v.deg(w), C, st.csize[depth], Cn);
+        const uint32_t nn =
+            warp_intersect16(v.list(w), v.deg(w), C + pos + 1, st.csize[depth] - pos - 1, Cn);
         if (lane == 0) st.csize[depth + 1] = nn;
         __syncwarp();
         const uint32_t l = k - 2 - (uint32_t)depth;  // level of the child
@@ -494,11 +590,24 @@ __device__ void ldfs_child(const LView &v, uint32_t p0, const LStack &st, const 
 
 // Warp per root (d+ <= 128): bit-row build in shared memory, padded lists,
 // then the root's children in turn.
+// Rank of member i of N+_u (ascending ids nbr[]) in the DAG order (key, id):
+// members with a smaller key, plus earlier members with the same key.
+__device__ __forceinline__ uint32_t dag_rank(const uint32_t *keys, uint32_t d, uint32_t i) {
+    const uint32_t ki = keys[i];
+    uint32_t r = 0;
+    for (uint32_t j = 0; j < d; j++) {
+        const uint32_t kj = keys[j];
+        r += (kj < ki) | ((kj == ki) & (j < i));
+    }
+    return r;
+}
+
 template <bool LIST>
 __device__ void sdegree_root_local(uint32_t u, uint32_t k, uint32_t D, const uint32_t *__restrict__ optr,
-                                   const uint32_t *__restrict__ oadj, uint32_t *S, const Emit &em,
-                                   DevResult *res, unsigned long long &cnt, unsigned long long &cks) {
-    const LLay L = make_llayout(D, k);
+                                   const uint32_t *__restrict__ oadj, const uint32_t *__restrict__ key,
+                                   uint32_t *S, const Emit &em, DevResult *res, uint32_t gallop,
+                                   unsigned long long &cnt, unsigned long long &cks) {
+    const LLay L = make_llayout(D, k, LIST);
     const unsigned lane = lane_id();
     uint32_t *nbr = S + L.NBR;
     uint32_t *lofs = S + L.LOFS;
@@ -507,9 +616,10 @@ __device__ void sdegree_root_local(uint32_t u, uint32_t k, uint32_t D, const uin
     uint32_t *hk = S + L.HK;
     uint16_t *hv = reinterpret_cast<uint16_t *>(S + L.HV);
     uint16_t *len = reinterpret_cast<uint16_t *>(S + L.LEN);
+    uint16_t *rk = reinterpret_cast<uint16_t *>(S + L.RK);
     uint32_t *bits = S + L.BITS;
     uint16_t *ladj = reinterpret_cast<uint16_t *>(S + L.LADJ);
-    const LStack st = stack_ptrs(S + L.STACK, D, k);
+    const LStack st = stack_ptrs(S + L.STACK, D, k, LIST);
 
     const uint32_t base = optr[u];
     const uint32_t d = optr[u + 1] - base;
@@ -522,6 +632,7 @@ __device__ void sdegree_root_local(uint32_t u, uint32_t k, uint32_t D, const uin
             uint32_t r0 = optr[v];
             rs[i] = r0;
             x = optr[v + 1] - r0;
+            lofs[i] = key[v];  // keys until the list offsets are laid out
         }
         uint32_t incl = x;
 #pragma unroll
@@ -537,6 +648,10 @@ __device__ void sdegree_root_local(uint32_t u, uint32_t k, uint32_t D, const uin
     __syncwarp();
     const uint32_t total = running;
     const uint32_t lo_id = nbr[0], hi_id = nbr[d - 1];
+    // local index = rank in the DAG order, so every reduced out-list L(i)
+    // holds only indices above i
+    for (uint32_t i = lane; i < d; i += 32) rk[i] = (uint16_t)dag_rank(lofs, d, i);
+    __syncwarp();
 
     // directed bit-rows: the members' out-lists are streamed as one flattened
     // sequence; a hash probe into N+_u finds the local index of each entry
@@ -552,11 +667,17 @@ __device__ void sdegree_root_local(uint32_t u, uint32_t k, uint32_t D, const uin
             uint32_t x = oadj[rs[a] + (e - pre[a])];
             if (x >= lo_id && x <= hi_id) {
                 int j = hash_find(hk, hv, T, hshift, x);
-                if (j >= 0) atomicOr(&bits[a * L.WPD + ((uint32_t)j >> 5)], 1u << (j & 31));
+                if (j >= 0) {
+                    const uint32_t jr = rk[j];
+                    atomicOr(&bits[rk[a] * L.WPD + (jr >> 5)], 1u << (jr & 31));
+                }
             }
         }
         a0 = __shfl_sync(kFull, a, 31);
     }
+    __syncwarp();
+    // member ids by local index (rs is free after the build)
+    for (uint32_t i = lane; i < d; i += 32) rs[rk[i]] = nbr[i];
     __syncwarp();
     // lengths -> padded offsets -> lists in ascending order
     running = 0;
@@ -592,10 +713,10 @@ __device__ void sdegree_root_local(uint32_t u, uint32_t k, uint32_t D, const uin
     __syncwarp();
 
     if (LIST && em.idmap) {  // output ids (batched unions map back to each graph's ids)
-        for (uint32_t i = lane; i < d; i += 32) nbr[i] = em.idmap[nbr[i]];
+        for (uint32_t i = lane; i < d; i += 32) rs[i] = em.idmap[rs[i]];
         __syncwarp();
     }
-    const LView v{nbr, lofs, len, ladj, d, (LIST && em.idmap) ? em.idmap[u] : u, k};
+    const LView v{rs, lofs, len, ladj, d, (LIST && em.idmap) ? em.idmap[u] : u, k, gallop};
     if (k == 3) {
         // C = all of N+_u: every edge of the reduced DAG closes a triangle
         if (!LIST) {
@@ -614,12 +735,211 @@ __device__ void sdegree_root_local(uint32_t u, uint32_t k, uint32_t D, const uin
         if (v.deg(w) + 2 >= k) ldfs_child<LIST>(v, w, st, em, res, cnt, cks);
 }
 
+// ------------------------------------- bit-row form of SDegreeList
+// For dense subproblems the reduced out-lists take more room than the
+// directed bit-rows of the same DAG (16 bits per edge against 1 bit per
+// pair), and lists that spill to global memory are slow to merge.  The CTA
+// form can then run SDegreeList on the bit-rows instead: C is a bitmap over
+// the local indices, C' = N+_v intersect C is one AND per word, |C'| a POPC,
+// and the degree prune and size tests are the same as with lists.  Local
+// indices follow the DAG order, so row(v) holds only indices above v and the
+// AND for candidate v starts at v's 4-word chunk.
+struct BView {
+    const uint32_t *R;    // bit-rows, stride WP words (16-byte aligned rows)
+    const uint32_t *ids;  // local index -> output id
+    uint32_t d, W, WP, u, k;  // W: words per row, a multiple of 4
+};
+
+__host__ __device__ inline uint32_t bstack_words(uint32_t W, uint32_t k) {
+    // C and P per depth (2 k W), path and cursor (2 k), sortedR (32), queue (32)
+    return (k * (2 * W + 2) + 64 + 3) & ~3u;
+}
+
+// |row(q) & C|; C is zero beyond its W words and row(q) below q's chunk
+__device__ __forceinline__ uint32_t brow_and(const BView &v, uint32_t q, const uint32_t *C) {
+    const uint4 *r4 = reinterpret_cast<const uint4 *>(v.R + q * v.WP);
+    const uint4 *c4 = reinterpret_cast<const uint4 *>(C);
+    uint32_t x = 0;
+    for (uint32_t t = q >> 7; t < (v.W >> 2); t++) {
+        const uint4 a = r4[t], b = c4[t];
+        x += __popc(a.x & b.x) + __popc(a.y & b.y) + __popc(a.z & b.z) + __popc(a.w & b.w);
+    }
+    return x;
+}
+
+// Leaf (l = 2) on bitmap C: every candidate q in C closes |row(q) & C|
+// cliques; candidates are packed 32 to a batch (queue of 64 u16).
+template <bool LIST>
+__device__ void bleaf_batch(const BView &v, const uint32_t *C, const uint16_t *q, uint32_t nb,
+                            const uint32_t *sortedR, const Emit &em, DevResult *res,
+                            unsigned long long &cnt, unsigned long long &cks) {
+    const unsigned lane = lane_id();
+    uint32_t x = lane < nb ? brow_and(v, q[lane], C) : 0u;
+    cnt += x;
+    if (!LIST) return;
+    // clique r of the batch: the lane o whose prefix holds it, and the
+    // (r - excl_o)-th set bit of row(q[o]) & C
+    const uint32_t incl = warp_incl_scan(x);
+    const uint32_t excl = incl - x;
+    const uint32_t tot = __shfl_sync(kFull, incl, 31);
+    unsigned long long slot0 = 0;
+    if (tot && em.ring) {
+        if (lane == 0) slot0 = atomicAdd(&res->emitted, (unsigned long long)tot);
+        slot0 = __shfl_sync(kFull, slot0, 0);
+    }
+    const uint32_t k = v.k;
+    for (uint32_t base = 0; base < tot; base += 32) {
+        const uint32_t r = base + lane;
+        uint32_t o = 0;
+#pragma unroll
+        for (uint32_t step = 16; step > 0; step >>= 1) {
+            const uint32_t vv = __shfl_sync(kFull, incl, o + step - 1);
+            if (vv <= r) o += step;
+        }
+        const uint32_t eo = __shfl_sync(kFull, excl, o & 31u);
+        if (r >= tot) continue;
+        const uint32_t qo = q[o];
+        const uint32_t *row = v.R + qo * v.WP;
+        uint32_t rank = r - eo, t2 = 0;
+        for (uint32_t t = qo >> 5; t < v.W; t++) {
+            const uint32_t mm = row[t] & C[t];
+            const uint32_t c = __popc(mm);
+            if (rank < c) {
+                t2 = t * 32 + __fns(mm, 0, (int)rank + 1);
+                break;
+            }
+            rank -= c;
+        }
+        const uint32_t a = v.ids[qo], b = v.ids[t2];
+        uint32_t ex[2] = {a < b ? a : b, a < b ? b : a};
+        uint32_t rec[KCL_MAX_K];
+        uint32_t nr = k - 2, ri = 0, ei = 0, oo = 0;
+        while (ri < nr || ei < 2) {
+            uint32_t rr = ri < nr ? sortedR[ri] : 0xFFFFFFFFu;
+            if (ei < 2 && ex[ei] < rr) rec[oo++] = ex[ei++];
+            else rec[oo++] = sortedR[ri++];
+        }
+        uint64_t h = hash_seed(k);
+        for (uint32_t z = 0; z < k; z++) h = mix64(h ^ (uint64_t)rec[z]);
+        cks += h;
+        if (em.ring) {
+            unsigned long long sl = slot0 + r;
+            bool ok = true;
+            if (em.wrap) sl %= em.capacity;
+            else ok = sl < em.capacity;
+            if (ok)
+                for (uint32_t z = 0; z < k; z++) em.ring[sl * k + z] = rec[z];
+        }
+    }
+}
+
+template <bool LIST>
+__device__ void bleaf(const BView &v, const uint32_t *C, uint32_t depth, const uint32_t *path,
+                      uint32_t *sortedR, const Emit &em, DevResult *res, unsigned long long &cnt,
+                      unsigned long long &cks) {
+    const unsigned lane = lane_id();
+    uint16_t *q = reinterpret_cast<uint16_t *>(sortedR + 32);
+    if (LIST) {
+        if (lane == 0) {
+            sortedR[0] = v.u;
+            for (uint32_t t = 1; t <= depth; t++) {
+                uint32_t x = v.ids[path[t]], j = t;
+                while (j > 0 && sortedR[j - 1] > x) { sortedR[j] = sortedR[j - 1]; j--; }
+                sortedR[j] = x;
+            }
+        }
+        __syncwarp();
+    }
+    uint32_t pend = 0;
+    for (uint32_t j = 0; j < v.W; j++) {
+        const uint32_t m = C[j];
+        if (!m) continue;
+        if ((m >> lane) & 1u) q[pend + __popc(m & ((1u << lane) - 1u))] = (uint16_t)(j * 32 + lane);
+        pend += __popc(m);
+        if (pend >= 32) {
+            __syncwarp();
+            bleaf_batch<LIST>(v, C, q, 32, sortedR, em, res, cnt, cks);
+            __syncwarp();
+            if (lane < pend - 32) q[lane] = q[32 + lane];
+            pend -= 32;
+            __syncwarp();
+        }
+    }
+    if (pend) {
+        __syncwarp();
+        bleaf_batch<LIST>(v, C, q, pend, sortedR, em, res, cnt, cks);
+        __syncwarp();
+    }
+}
+
+// Inner node at level l on bitmap C: P = the candidates q with
+// |row(q) & C| >= l-1.
+__device__ void bexpand(const BView &v, const uint32_t *C, uint32_t l, uint32_t *P) {
+    const unsigned lane = lane_id();
+    for (uint32_t j = 0; j < v.W; j++) {
+        const uint32_t m = C[j];
+        bool ok = false;
+        if ((m >> lane) & 1u) ok = brow_and(v, j * 32 + lane, C) + 1 >= l;
+        const unsigned bal = __ballot_sync(kFull, ok);
+        if (lane == 0) P[j] = bal;
+    }
+    __syncwarp();
+}
+
+// The subtree below first-level child p0 (C1 = row(p0)), one warp.
+template <bool LIST>
+__device__ void bdfs_child(const BView &v, uint32_t p0, uint32_t *stack, const Emit &em,
+                           DevResult *res, unsigned long long &cnt, unsigned long long &cks) {
+    const unsigned lane = lane_id();
+    const uint32_t W = v.W, k = v.k;
+    uint32_t *Cst = stack;
+    uint32_t *Pst = Cst + k * W;
+    uint32_t *path = Pst + k * W;
+    uint32_t *cur = path + k;
+    uint32_t *sortedR = cur + k;
+    for (uint32_t t = lane; t < W; t += 32) Cst[W + t] = v.R[p0 * v.WP + t];
+    if (lane == 0) path[1] = p0;
+    __syncwarp();
+    if (k - 2 == 2) {
+        bleaf<LIST>(v, Cst + W, 1, path, sortedR, em, res, cnt, cks);
+        return;
+    }
+    bexpand(v, Cst + W, k - 2, Pst + W);
+    if (lane == 0) cur[1] = 0;
+    __syncwarp();
+    int depth = 1;
+    while (depth >= 1) {
+        uint32_t *P = Pst + depth * W;
+        uint32_t j = cur[depth];
+        while (j < W && P[j] == 0) j++;
+        if (j >= W) { depth--; continue; }
+        const uint32_t pw = P[j];
+        const uint32_t p = j * 32 + (__ffs(pw) - 1);
+        __syncwarp();
+        if (lane == 0) { P[j] = pw & (pw - 1); cur[depth] = j; path[depth + 1] = p; }
+        const uint32_t *C = Cst + depth * W;
+        uint32_t *Cn = Cst + (depth + 1) * W;
+        for (uint32_t t = lane; t < W; t += 32) Cn[t] = v.R[p * v.WP + t] & C[t];
+        __syncwarp();
+        const uint32_t lc = k - 2 - (uint32_t)depth;  // level of the child
+        if (lc == 2) {
+            bleaf<LIST>(v, Cn, depth + 1, path, sortedR, em, res, cnt, cks);
+            __syncwarp();
+        } else {
+            bexpand(v, Cn, lc, Pst + (depth + 1) * W);
+            if (lane == 0) cur[depth + 1] = 0;
+            __syncwarp();
+            depth++;
+        }
+    }
+}
+
 // ------------------------------------------------ CTA per root (d+ > 128)
 // Shared region (words) of the CTA form; the reduced lists and the per-warp
 // stacks follow it in shared memory (lists move to the global arena when
 // they do not leave room for enough warps).
 struct CLay {
-    uint32_t D, WPD, NBR, RS, PRE, LOFS, HK, HV, LEN, P0, META, total;
+    uint32_t D, WPD, NBR, RS, PRE, LOFS, HK, HV, LEN, RK, P0, META, total;
 };
 
 __host__ __device__ inline CLay make_clayout(uint32_t D) {
@@ -634,7 +954,8 @@ __host__ __device__ inline CLay make_clayout(uint32_t D) {
     L.HK = L.LOFS + D + 1;     // 2D
     L.HV = L.HK + 2 * D;       // 2D u16
     L.LEN = L.HV + D;          // D u16: list lengths
-    L.P0 = L.LEN + D / 2;      // D u16: first-level children
+    L.RK = L.LEN + D / 2;      // D u16: DAG rank of each member
+    L.P0 = L.RK + D / 2;       // D u16: first-level children
     L.META = L.P0 + D / 2;     // 16 words
     L.total = (L.META + 16 + 3) & ~3u;
     return L;
@@ -651,10 +972,12 @@ __host__ __device__ inline size_t cta_arena_words(uint32_t D) {
 template <bool LIST>
 __global__ void __launch_bounds__(512) k_sdegree_cta(uint32_t k, uint32_t D, const uint32_t *__restrict__ optr,
                                                     const uint32_t *__restrict__ oadj,
+                                                    const uint32_t *__restrict__ key,
                                                     const uint32_t *__restrict__ roots, uint32_t begin,
                                                     uint32_t end, unsigned *queue, uint32_t *arena,
-                                                    uint32_t smem_words, Emit em,
-                                                    unsigned long long *per_root, DevResult *res) {
+                                                    uint32_t smem_words, Emit em, uint32_t gallop,
+                                                    uint32_t bitmap, unsigned long long *per_root,
+                                                    DevResult *res) {
     extern __shared__ uint32_t smem[];
     const CLay L = make_clayout(D);
     const uint32_t tid = threadIdx.x, nth = blockDim.x, lane = lane_id(), warp = tid >> 5;
@@ -666,6 +989,7 @@ __global__ void __launch_bounds__(512) k_sdegree_cta(uint32_t k, uint32_t D, con
     uint32_t *hk = smem + L.HK;
     uint16_t *hv = reinterpret_cast<uint16_t *>(smem + L.HV);
     uint16_t *len = reinterpret_cast<uint16_t *>(smem + L.LEN);
+    uint16_t *rk = reinterpret_cast<uint16_t *>(smem + L.RK);
     uint16_t *p0 = reinterpret_cast<uint16_t *>(smem + L.P0);
     uint32_t *meta = smem + L.META;
     uint32_t *slice = arena + (size_t)blockIdx.x * cta_arena_words(D);
@@ -689,6 +1013,7 @@ __global__ void __launch_bounds__(512) k_sdegree_cta(uint32_t k, uint32_t D, con
             uint32_t r0 = optr[x];
             rs[i] = r0;
             pre[i] = optr[x + 1] - r0;
+            lofs[i] = key[x];  // keys until the list offsets are laid out
         }
         uint32_t T, hshift;
         hash_size(d, &T, &hshift);
@@ -712,10 +1037,14 @@ __global__ void __launch_bounds__(512) k_sdegree_cta(uint32_t k, uint32_t D, con
             }
             if (lane == 0) pre[d] = running;
         }
+        // local index = rank in the DAG order, so every reduced out-list L(i)
+        // holds only indices above i; the hash maps an id to its rank
         for (uint32_t i = tid; i < d; i += nth) {
-            uint32_t key = nbr[i], h = hash_slot(key, hshift);
-            while (atomicCAS(&hk[h], kHashEmpty, key) != kHashEmpty) h = (h + 1) & (T - 1);
-            hv[h] = (uint16_t)i;
+            const uint32_t r = dag_rank(lofs, d, i);
+            rk[i] = (uint16_t)r;
+            uint32_t id = nbr[i], h = hash_slot(id, hshift);
+            while (atomicCAS(&hk[h], kHashEmpty, id) != kHashEmpty) h = (h + 1) & (T - 1);
+            hv[h] = (uint16_t)r;
         }
         __syncthreads();
         // ---- directed bit-rows: bit j of row i iff member j is in N+_{v_i}
@@ -736,11 +1065,13 @@ __global__ void __launch_bounds__(512) k_sdegree_cta(uint32_t k, uint32_t D, con
                 uint32_t x = oadj[rs[a] + (e - pre[a])];
                 if (x >= lo_id && x <= hi_id) {
                     int j = hash_find(hk, hv, T, hshift, x);
-                    if (j >= 0) atomicOr(&bits[a * L.WPD + ((uint32_t)j >> 5)], 1u << (j & 31));
+                    if (j >= 0) atomicOr(&bits[rk[a] * L.WPD + ((uint32_t)j >> 5)], 1u << (j & 31));
                 }
             }
         }
         __syncthreads();
+        // member ids by local index (rs is free after the build)
+        for (uint32_t i = tid; i < d; i += nth) rs[rk[i]] = nbr[i];
         // ---- row lengths, longest row, padded offsets
         for (uint32_t i = tid; i < d; i += nth) {
             uint32_t c = 0;
@@ -767,7 +1098,7 @@ __global__ void __launch_bounds__(512) k_sdegree_cta(uint32_t k, uint32_t D, con
                 // place the lists and size the stacks: lists in shared memory
                 // unless that would leave fewer than min(8, possible) warps
                 uint32_t cap = meta[3] ? meta[3] : 1;
-                uint32_t sw = stack_words(cap, k);
+                uint32_t sw = stack_words(cap, k, LIST);
                 uint32_t budget = smem_words - L.total;
                 uint32_t lw = (lofs[d] / 2 + 3) & ~3u;
                 uint32_t nw_g = budget / sw;
@@ -780,12 +1111,39 @@ __global__ void __launch_bounds__(512) k_sdegree_cta(uint32_t k, uint32_t D, con
                 meta[5] = in_smem ? nw_s : nw_g;
                 meta[6] = sw;
                 meta[7] = in_smem ? lw : 0u;  // stacks start after the lists
+                // bit-row form instead, when the rows fit with enough warps
+                // and the lists would take more than threshold/16 of their room
+                const uint32_t Wb = round4((d + 31) >> 5);
+                const uint32_t WPB = ((Wb >> 2) & 1) ? Wb : Wb + 4;
+                const uint32_t bw = d * WPB, bsw = bstack_words(Wb, k);
+                uint32_t nw_b = bw <= budget ? (budget - bw) / bsw : 0;
+                if (nw_b > nwarps) nw_b = nwarps;
+                const uint32_t thr = bitmap ? bitmap : 16u;
+                if (k > 3 && bitmap != 0xFFFFFFFFu && nw_b >= want && nw_b >= 1 &&
+                    16ull * lw > (unsigned long long)thr * bw) {
+                    meta[4] = 2u;
+                    meta[5] = nw_b;
+                    meta[6] = bsw;
+                    meta[7] = bw;  // stacks start after the rows
+                    meta[10] = Wb;
+                    meta[11] = WPB;
+                }
             }
         }
         __syncthreads();
-        uint16_t *ladj = meta[4] ? reinterpret_cast<uint16_t *>(smem + L.total) : ladj_g;
+        const bool bitrows = meta[4] == 2u;
+        uint16_t *ladj = meta[4] == 1u ? reinterpret_cast<uint16_t *>(smem + L.total) : ladj_g;
+        if (bitrows) {
+            // rows to shared memory, zero beyond the row's words
+            const uint32_t Wb = meta[10], WPB = meta[11];
+            uint32_t *R = smem + L.total;
+            for (uint32_t e = tid; e < d * Wb; e += nth) {
+                const uint32_t i = e / Wb, t = e - i * Wb;
+                R[i * WPB + t] = t < L.WPD ? bits[i * L.WPD + t] : 0u;
+            }
+        }
         // ---- extraction: row i's bits in ascending order -> L(i), padded
-        for (uint32_t i = tid; i < d; i += nth) {
+        for (uint32_t i = bitrows ? d : tid; i < d; i += nth) {
             uint32_t o = lofs[i];
             for (uint32_t t = 0; t < L.WPD; t++) {
                 uint32_t m = bits[i * L.WPD + t];
@@ -799,8 +1157,8 @@ __global__ void __launch_bounds__(512) k_sdegree_cta(uint32_t k, uint32_t D, con
         const uint32_t nw_dfs = meta[5], sw = meta[6];
         if (nw_dfs == 0 && tid == 0) atomicOr(&res->status, DEV_ERR_INTERNAL);  // no stack fits
         if (LIST && em.idmap)  // output ids (batched unions map back to each graph's ids)
-            for (uint32_t i = tid; i < d; i += nth) nbr[i] = em.idmap[nbr[i]];
-        const LView v{nbr, lofs, len, ladj, d, (LIST && em.idmap) ? em.idmap[u] : u, k};
+            for (uint32_t i = tid; i < d; i += nth) rs[i] = em.idmap[rs[i]];
+        const LView v{rs, lofs, len, ladj, d, (LIST && em.idmap) ? em.idmap[u] : u, k, gallop};
         const uint32_t cap = meta[3] ? meta[3] : 1;
         // ---- first-level children (|L(w)| >= k-2), longest lists first
         if (k > 3 && warp == 0) {
@@ -827,8 +1185,19 @@ __global__ void __launch_bounds__(512) k_sdegree_cta(uint32_t k, uint32_t D, con
             for (uint32_t i = tid; i < round4(d); i += nth) p0[i] = i < d ? (uint16_t)i : kPad;
         }
         __syncthreads();
-        if (warp < nw_dfs) {
-            const LStack st = stack_ptrs(smem + L.total + meta[7] + warp * sw, cap < d ? cap : d, k);
+        if (bitrows && warp < nw_dfs) {
+            const BView bv{smem + L.total, rs, d, meta[10], meta[11], v.u, k};
+            uint32_t *stack = smem + L.total + meta[7] + warp * sw;
+            const uint32_t n0 = meta[8];
+            for (;;) {
+                uint32_t i = 0;
+                if (lane == 0) i = atomicAdd(&meta[9], 1u);
+                i = __shfl_sync(kFull, i, 0);
+                if (i >= n0) break;
+                bdfs_child<LIST>(bv, p0[i], stack, em, res, cnt, cks);
+            }
+        } else if (warp < nw_dfs) {
+            const LStack st = stack_ptrs(smem + L.total + meta[7] + warp * sw, cap < d ? cap : d, k, LIST);
             if (k == 3) {
                 if (!LIST) {
                     uint32_t c = 0;
@@ -876,9 +1245,10 @@ __global__ void __launch_bounds__(512) k_sdegree_cta(uint32_t k, uint32_t D, con
 template <bool LIST, bool GLOBAL, bool LOCAL>
 __global__ void __launch_bounds__(128) k_sdegree(uint32_t k, uint32_t D, const uint32_t *__restrict__ optr,
                                                 const uint32_t *__restrict__ oadj,
+                                                const uint32_t *__restrict__ key,
                                                 const uint32_t *__restrict__ roots, uint32_t begin,
                                                 uint32_t end, unsigned *queue, uint32_t *arena,
-                                                uint32_t words_per_warp, Emit em,
+                                                uint32_t words_per_warp, Emit em, uint32_t gallop,
                                                 unsigned long long *per_root, DevResult *res) {
     extern __shared__ uint32_t smem[];
     const unsigned lane = lane_id();
@@ -894,7 +1264,7 @@ __global__ void __launch_bounds__(128) k_sdegree(uint32_t k, uint32_t D, const u
         uint32_t u = roots[begin + idx];
         unsigned long long before = cnt;
         const unsigned long long before_cks = cks;
-        if (LOCAL) sdegree_root_local<LIST>(u, k, D, optr, oadj, S, em, res, cnt, cks);
+        if (LOCAL) sdegree_root_local<LIST>(u, k, D, optr, oadj, key, S, em, res, gallop, cnt, cks);
         else sdegree_root<LIST>(u, k, D, optr, oadj, S, em, res, cnt, cks);
         if (per_root) {
             unsigned long long mine = cnt - before;
@@ -933,8 +1303,8 @@ int cta_threads(uint32_t D) { return D <= 128 ? 128 : 512; }
 template <bool LIST>
 void launch_warp_local(uint32_t k, uint32_t D, Workspace &w, uint32_t begin, uint32_t end,
                        unsigned *queue, const Emit &em, unsigned long long *per_root, int num_sms,
-                       cudaStream_t s) {
-    uint32_t words = make_llayout(D, k).total;
+                       uint32_t gallop, cudaStream_t s) {
+    uint32_t words = make_llayout(D, k, LIST).total;
     int wpb = (int)(kSmemPerBlock / ((size_t)words * 4));
     if (wpb > 4) wpb = 4;
     if (wpb < 1) wpb = 1;
@@ -948,13 +1318,14 @@ void launch_warp_local(uint32_t k, uint32_t D, Workspace &w, uint32_t begin, uin
     uint32_t blocks = (uint32_t)num_sms * occ;
     uint32_t need = (end - begin + wpb - 1) / wpb;
     if (blocks > need) blocks = need;
-    kern<<<blocks, wpb * 32, smem, s>>>(k, D, w.optr, w.oadj, w.roots, begin, end, queue, w.arena,
-                                        words, em, per_root, w.res);
+    kern<<<blocks, wpb * 32, smem, s>>>(k, D, w.optr, w.oadj, w.key, w.roots, begin, end, queue,
+                                        w.arena, words, em, gallop, per_root, w.res);
 }
 
 template <bool LIST>
 void launch_cta(uint32_t k, uint32_t D, Workspace &w, uint32_t begin, uint32_t end, unsigned *queue,
-                const Emit &em, unsigned long long *per_root, int num_sms, cudaStream_t s) {
+                const Emit &em, unsigned long long *per_root, int num_sms, uint32_t gallop,
+                uint32_t bitmap, cudaStream_t s) {
     size_t smem = cta_smem_bytes(D);
     const int threads = cta_threads(D);
     auto kern = k_sdegree_cta<LIST>;
@@ -966,19 +1337,21 @@ void launch_cta(uint32_t k, uint32_t D, Workspace &w, uint32_t begin, uint32_t e
     if (occ > 2) occ = 2;  // the arena holds two slices per SM
     uint32_t blocks = (uint32_t)num_sms * occ;
     if (blocks > end - begin) blocks = end - begin;
-    kern<<<blocks, threads, smem, s>>>(k, D, w.optr, w.oadj, w.roots, begin, end, queue, w.arena,
-                                       (uint32_t)(smem / 4), em, per_root, w.res);
+    kern<<<blocks, threads, smem, s>>>(k, D, w.optr, w.oadj, w.key, w.roots, begin, end, queue,
+                                       w.arena, (uint32_t)(smem / 4), em, gallop, bitmap, per_root,
+                                       w.res);
 }
 
 template <bool LIST>
 void launch_global_lists(uint32_t k, uint32_t D, Workspace &w, uint32_t begin, uint32_t end,
                          unsigned *queue, const Emit &em, unsigned long long *per_root, int num_sms,
-                         cudaStream_t s) {
+                         uint32_t gallop, cudaStream_t s) {
     uint32_t words = make_slayout(D, k).total;
     uint32_t blocks = (uint32_t)num_sms;
     if (blocks * 2 > end - begin) blocks = (end - begin + 1) / 2;
-    k_sdegree<LIST, true, false><<<blocks, 64, 0, s>>>(k, D, w.optr, w.oadj, w.roots, begin, end,
-                                                       queue, w.arena, words, em, per_root, w.res);
+    k_sdegree<LIST, true, false><<<blocks, 64, 0, s>>>(k, D, w.optr, w.oadj, w.key, w.roots, begin,
+                                                       end, queue, w.arena, words, em, gallop, per_root,
+                                                       w.res);
 }
 
 }  // namespace
@@ -1013,18 +1386,21 @@ int launch_sdegree(const kcl_graph *g, uint32_t k, Workspace &w, const uint32_t 
         if (end <= begin) continue;
         uint32_t D = kClassD[c];
         unsigned *q = w.queue + c;
+        const uint32_t gl = la.listing ? g->tuning.sdegree_gallop_list[c] : g->tuning.sdegree_gallop[c];
+        const uint32_t bm = g->tuning.sdegree_bitmap[c];
+        const int ns = g->num_sms;
         class_mark(la, c, 0, s);
         if (c < kWarpClasses) {
             // listing hashes every clique: a root's cost grows with its clique
             // count, so listing shares each root's children over a CTA of 4 warps
-            if (la.listing) launch_cta<true>(k, D, w, begin, end, q, em, la.per_root, g->num_sms, s);
-            else launch_warp_local<false>(k, D, w, begin, end, q, em, la.per_root, g->num_sms, s);
+            if (la.listing) launch_cta<true>(k, D, w, begin, end, q, em, la.per_root, ns, gl, bm, s);
+            else launch_warp_local<false>(k, D, w, begin, end, q, em, la.per_root, ns, gl, s);
         } else if (c < kCtaClasses) {
-            if (la.listing) launch_cta<true>(k, D, w, begin, end, q, em, la.per_root, g->num_sms, s);
-            else launch_cta<false>(k, D, w, begin, end, q, em, la.per_root, g->num_sms, s);
+            if (la.listing) launch_cta<true>(k, D, w, begin, end, q, em, la.per_root, ns, gl, bm, s);
+            else launch_cta<false>(k, D, w, begin, end, q, em, la.per_root, ns, gl, bm, s);
         } else {
-            if (la.listing) launch_global_lists<true>(k, D, w, begin, end, q, em, la.per_root, g->num_sms, s);
-            else launch_global_lists<false>(k, D, w, begin, end, q, em, la.per_root, g->num_sms, s);
+            if (la.listing) launch_global_lists<true>(k, D, w, begin, end, q, em, la.per_root, ns, gl, s);
+            else launch_global_lists<false>(k, D, w, begin, end, q, em, la.per_root, ns, gl, s);
         }
         class_mark(la, c, 1, s);
         launches++;

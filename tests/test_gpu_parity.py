@@ -322,3 +322,98 @@ def test_rmat20_full_size_counts(kcl, rmat20, k):
         fn = _oracle_mode(o)
         ref = fn(rp, col, k, roots=sample, per_root=True, count_only=True)["per_root"]
         assert np.array_equal(per[sample], ref[sample]), o
+
+
+# ------------------------------------------- leaf forms and the autotuner
+@pytest.mark.parametrize("gallop", [0, 4_000_000_000])
+def test_sdegree_leaf_forms_agree(kcl, small_workload, gallop):
+    """SDegree's leaf by merges only (0) and by galloping only (a threshold
+    no estimate reaches): identical counts, checksums and listings."""
+    rp, col = small_workload
+    g = kcl.kcl_load_csr(rp, col)
+    kcl.kcl_set_tuning(g, {"sdegree_gallop": [gallop] * kcl.KCL_MAX_CLASSES,
+                           "sdegree_gallop_list": [gallop] * kcl.KCL_MAX_CLASSES})
+    for k in (3, 4, 6):
+        ref_c, ref_s = oracle.plain(rp, col, k)
+        assert kcl.kcl_count(g, k, "degree") == ref_c
+        assert kcl.kcl_list(g, k, "degree", None)[:2] == (ref_c, ref_s)
+    dense = kclgen.chung_lu(3000, 12000, 2.3, groups=3, group_size=(260, 260), group_p=0.45, seed=260)
+    g2 = kcl.kcl_load_csr(*dense)
+    kcl.kcl_set_tuning(g2, {"sdegree_gallop": [gallop] * kcl.KCL_MAX_CLASSES,
+                            "sdegree_gallop_list": [gallop] * kcl.KCL_MAX_CLASSES})
+    for k in (4, 5):
+        ref = oracle.plain(*dense, k)
+        assert kcl.kcl_list(g2, k, "degree", None)[:2] == ref
+
+
+def test_autotune_keeps_results(kcl, small_workload):
+    rp, col = small_workload
+    g = kcl.kcl_load_csr(rp, col)
+    kcl.kcl_autotune(g, 5, "degree")
+    t = kcl.kcl_autotune(g, 4, "degree", listing=True)
+    assert kcl.kcl_get_tuning(g) == t
+    assert all(v in (0, 40, 80, 160, 400) for v in t["sdegree_gallop"] + t["sdegree_gallop_list"])
+    assert all(v in (0, 4, 64, 0xFFFFFFFF) for v in t["sdegree_bitmap"])
+    assert kcl.kcl_count(g, 5, "degree") == oracle.plain(rp, col, 5)[0]
+    assert kcl.kcl_list(g, 4, "degree", None)[:2] == oracle.plain(rp, col, 4)
+    assert kcl.kcl_autotune(g, 5, "color") == t
+
+
+# ------------------------------------------------------ ablation switches
+@pytest.mark.parametrize("flags", [1, 2, 4, 7])
+def test_ablation_switches_keep_results(kcl, small_workload, flags):
+    """Pre-Core, Pre-List and the colour prune off (alone and together):
+    counts, checksums and per-root sums stay exact."""
+    rp, col = small_workload
+    g = kcl.kcl_load_csr(rp, col)
+    kcl.kcl_set_options(g, flags)
+    assert kcl.kcl_get_options(g) == flags
+    for k in (3, 5, 8):
+        ref = oracle.plain(rp, col, k)
+        for o in ORDS:
+            assert kcl.kcl_count(g, k, o) == ref[0], (k, o)
+            assert kcl.kcl_list(g, k, o, None)[:2] == ref, (k, o)
+    st = kcl.kcl_stage_info(g, 5, "color")
+    if flags & kcl.KCL_OPT_NO_PRECORE and flags & kcl.KCL_OPT_NO_PRELIST:
+        assert st["alive_final"].all() and st["prelist_count"] == 0
+
+
+def test_ablation_rejects_unknown_bits(kcl, fig1):
+    g = kcl.kcl_load_csr(*fig1)
+    with pytest.raises(kcl.KclError):
+        kcl.kcl_set_options(g, 8)
+
+
+def test_scratch_bytes_grow_with_the_call(kcl, small_workload):
+    rp, col = small_workload
+    g = kcl.kcl_load_csr(rp, col)
+    assert kcl.kcl_scratch_bytes(g)[1] == 0  # loading validates with the workspace; no arena yet
+    kcl.kcl_count(g, 4, "degree")
+    ws, ar = kcl.kcl_scratch_bytes(g)
+    n, nnz = len(rp) - 1, len(col)
+    assert 70 * n + 2 * nnz <= ws <= 90 * n + 2 * nnz + (1 << 16)
+    assert ar > 0
+
+
+@pytest.mark.parametrize("bitmap", [1, 0xFFFFFFFF])
+def test_sdegree_bitrow_and_list_forms_agree(kcl, bitmap):
+    """SDegree's CTA classes on bit-rows (threshold 1: whenever the rows fit)
+    and on lists only: identical counts and checksums."""
+    tune = {"sdegree_bitmap": [bitmap] * kcl.KCL_MAX_CLASSES}
+    for n in (300, 700):
+        rp, col = _near_complete(n)
+        g = kcl.kcl_load_csr(rp, col)
+        kcl.kcl_set_tuning(g, tune)
+        for k in (4, 5) if n <= 300 else (4,):
+            want = math.comb(n, k) - math.comb(n - 2, k - 2)
+            assert kcl.kcl_count(g, k, "degree") == want
+            assert kcl.kcl_list(g, k, "degree", None)[0] == want
+    for size, p in ((170, 0.6), (260, 0.45)):
+        rp, col = kclgen.chung_lu(3000, 12000, 2.3, groups=3, group_size=(size, size), group_p=p,
+                                  seed=size)
+        g = kcl.kcl_load_csr(rp, col)
+        kcl.kcl_set_tuning(g, tune)
+        for k in (4, 5, 6):
+            ref = oracle.plain(rp, col, k)
+            assert kcl.kcl_count(g, k, "degree") == ref[0]
+            assert kcl.kcl_list(g, k, "degree", None)[:2] == ref
