@@ -377,6 +377,7 @@ __device__ void leaf_batch(const View &v, const uint32_t *C, uint32_t cw, const 
         if (lane == 0) slot0 = atomicAdd(&res->emitted, (unsigned long long)tot);
         slot0 = __shfl_sync(kFull, slot0, 0);
     }
+    const uint64_t seed = hash_seed(v.k);
     for (uint32_t base = 0; base < tot; base += 32) {
         const uint32_t r = base + lane;
         uint32_t o = 0;  // number of lanes whose inclusive prefix is <= r
@@ -400,27 +401,8 @@ __device__ void leaf_batch(const View &v, const uint32_t *C, uint32_t cw, const 
             }
             rank -= c;
         }
-        const uint32_t a = v.ids[po], b = v.ids[qq];
-        const uint32_t k = v.k;
-        uint32_t ex[2] = {a < b ? a : b, a < b ? b : a};
-        uint32_t rec[KCL_MAX_K];
-        uint32_t nr = k - 2, ri = 0, ei = 0, oo = 0;
-        while (ri < nr || ei < 2) {
-            uint32_t rr = ri < nr ? sortedR[ri] : 0xFFFFFFFFu;
-            if (ei < 2 && ex[ei] < rr) rec[oo++] = ex[ei++];
-            else rec[oo++] = sortedR[ri++];
-        }
-        uint64_t h = hash_seed(k);
-        for (uint32_t z = 0; z < k; z++) h = mix64(h ^ (uint64_t)rec[z]);
-        cks += h;
-        if (em.ring) {
-            unsigned long long sl = slot0 + r;
-            bool ok = true;
-            if (em.wrap) sl %= em.capacity;
-            else ok = sl < em.capacity;
-            if (ok)
-                for (uint32_t z = 0; z < k; z++) em.ring[sl * k + z] = rec[z];
-        }
+        cks += clique_hash2(sortedR, v.k - 2, v.ids[po], v.ids[qq], seed,
+                            ring_slot(em.ring, em.capacity, em.wrap, slot0 + r, v.k));
     }
 }
 

@@ -136,6 +136,48 @@ __device__ __forceinline__ uint64_t hash_seed(uint32_t k) {
 
 __device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
 
+// Hash of the clique R + {a, b} (a != b, neither in R): the SplitMix64
+// chain over its ids in ascending order, R's k-2 ids ascending in
+// sortedR[0..nr).  The ids are merged on the fly (no record array, so nothing
+// spills to local memory); when out is not null the ascending record is
+// written there (k ids).  seed = hash_seed(k).
+__device__ __forceinline__ uint64_t clique_hash2(const uint32_t *sortedR, uint32_t nr, uint32_t a,
+                                                 uint32_t b, uint64_t seed, uint32_t *out) {
+    const uint32_t lo = a < b ? a : b, hi = a < b ? b : a;
+    uint64_t h = seed;
+    uint32_t ri = 0, o = 0;
+    uint32_t x = ri < nr ? sortedR[ri] : 0xFFFFFFFFu;
+    while (x < lo) {
+        h = mix64(h ^ (uint64_t)x);
+        if (out) out[o++] = x;
+        x = ++ri < nr ? sortedR[ri] : 0xFFFFFFFFu;
+    }
+    h = mix64(h ^ (uint64_t)lo);
+    if (out) out[o++] = lo;
+    while (x < hi) {
+        h = mix64(h ^ (uint64_t)x);
+        if (out) out[o++] = x;
+        x = ++ri < nr ? sortedR[ri] : 0xFFFFFFFFu;
+    }
+    h = mix64(h ^ (uint64_t)hi);
+    if (out) out[o++] = hi;
+    while (ri < nr) {
+        h = mix64(h ^ (uint64_t)x);
+        if (out) out[o++] = x;
+        x = ++ri < nr ? sortedR[ri] : 0xFFFFFFFFu;
+    }
+    return h;
+}
+
+// Ring slot of a clique (null when it does not fit and the ring does not wrap).
+__device__ __forceinline__ uint32_t *ring_slot(uint32_t *ring, unsigned long long capacity, int wrap,
+                                               unsigned long long slot, uint32_t k) {
+    if (!ring) return nullptr;
+    if (wrap) slot %= capacity;
+    else if (slot >= capacity) return nullptr;
+    return ring + slot * k;
+}
+
 // Inclusive prefix sum over the 32 lanes of a warp (all lanes active).
 __device__ __forceinline__ uint32_t warp_incl_scan(uint32_t x) {
     const unsigned lane = lane_id();

@@ -70,26 +70,8 @@ __device__ void emit_matches(bool found, uint32_t w, uint32_t v, uint32_t k, con
         v = em.idmap[v];
         w = em.idmap[w];
     }
-    uint32_t e0 = v < w ? v : w, e1 = v < w ? w : v;
-    uint32_t ex[2] = {e0, e1};
-    uint32_t rec[KCL_MAX_K];
-    uint32_t nr = k - 2, ri = 0, ei = 0, o = 0;
-    while (ri < nr || ei < 2) {
-        uint32_t r = ri < nr ? sortedR[ri] : 0xFFFFFFFFu;
-        if (ei < 2 && ex[ei] < r) rec[o++] = ex[ei++];
-        else rec[o++] = sortedR[ri++];
-    }
-    uint64_t h = hash_seed(k);
-    for (uint32_t z = 0; z < k; z++) h = mix64(h ^ (uint64_t)rec[z]);
-    cks += h;
-    if (em.ring) {
-        unsigned long long sl = slot0 + __popc(m & ((1u << lane) - 1u));
-        bool ok = true;
-        if (em.wrap) sl %= em.capacity;
-        else ok = sl < em.capacity;
-        if (ok)
-            for (uint32_t z = 0; z < k; z++) em.ring[sl * k + z] = rec[z];
-    }
+    const unsigned long long sl = slot0 + __popc(m & ((1u << lane) - 1u));
+    cks += clique_hash2(sortedR, k - 2, v, w, hash_seed(k), ring_slot(em.ring, em.capacity, em.wrap, sl, k));
 }
 
 // C' = N+_v intersect C; writes C' (ascending) to `out` when non-null and
@@ -389,28 +371,11 @@ __device__ void flush_pairs(const LView &v, uint32_t nb, const LStack &st, const
         if (lane == 0) slot0 = atomicAdd(&res->emitted, (unsigned long long)nb);
         slot0 = __shfl_sync(kFull, slot0, 0);
     }
+    const uint64_t seed = hash_seed(k);
     for (uint32_t e = lane; e < nb; e += 32) {
         const uint32_t pr = st.ebuf[e];
-        const uint32_t va = v.nbr[pr >> 16], vb = v.nbr[pr & 0xFFFFu];
-        uint32_t ex[2] = {va < vb ? va : vb, va < vb ? vb : va};
-        uint32_t rec[KCL_MAX_K];
-        uint32_t nr = k - 2, ri = 0, ei = 0, o = 0;
-        while (ri < nr || ei < 2) {
-            uint32_t r = ri < nr ? st.sortedR[ri] : 0xFFFFFFFFu;
-            if (ei < 2 && ex[ei] < r) rec[o++] = ex[ei++];
-            else rec[o++] = st.sortedR[ri++];
-        }
-        uint64_t h = hash_seed(k);
-        for (uint32_t z = 0; z < k; z++) h = mix64(h ^ (uint64_t)rec[z]);
-        cks += h;
-        if (em.ring) {
-            unsigned long long sl = slot0 + e;
-            bool ok = true;
-            if (em.wrap) sl %= em.capacity;
-            else ok = sl < em.capacity;
-            if (ok)
-                for (uint32_t z = 0; z < k; z++) em.ring[sl * k + z] = rec[z];
-        }
+        cks += clique_hash2(st.sortedR, k - 2, v.nbr[pr >> 16], v.nbr[pr & 0xFFFFu], seed,
+                            ring_slot(em.ring, em.capacity, em.wrap, slot0 + e, k));
     }
     __syncwarp();
 }
@@ -788,6 +753,7 @@ __device__ void bleaf_batch(const BView &v, const uint32_t *C, const uint16_t *q
         slot0 = __shfl_sync(kFull, slot0, 0);
     }
     const uint32_t k = v.k;
+    const uint64_t seed = hash_seed(k);
     for (uint32_t base = 0; base < tot; base += 32) {
         const uint32_t r = base + lane;
         uint32_t o = 0;
@@ -810,26 +776,8 @@ __device__ void bleaf_batch(const BView &v, const uint32_t *C, const uint16_t *q
             }
             rank -= c;
         }
-        const uint32_t a = v.ids[qo], b = v.ids[t2];
-        uint32_t ex[2] = {a < b ? a : b, a < b ? b : a};
-        uint32_t rec[KCL_MAX_K];
-        uint32_t nr = k - 2, ri = 0, ei = 0, oo = 0;
-        while (ri < nr || ei < 2) {
-            uint32_t rr = ri < nr ? sortedR[ri] : 0xFFFFFFFFu;
-            if (ei < 2 && ex[ei] < rr) rec[oo++] = ex[ei++];
-            else rec[oo++] = sortedR[ri++];
-        }
-        uint64_t h = hash_seed(k);
-        for (uint32_t z = 0; z < k; z++) h = mix64(h ^ (uint64_t)rec[z]);
-        cks += h;
-        if (em.ring) {
-            unsigned long long sl = slot0 + r;
-            bool ok = true;
-            if (em.wrap) sl %= em.capacity;
-            else ok = sl < em.capacity;
-            if (ok)
-                for (uint32_t z = 0; z < k; z++) em.ring[sl * k + z] = rec[z];
-        }
+        cks += clique_hash2(sortedR, k - 2, v.ids[qo], v.ids[t2], seed,
+                            ring_slot(em.ring, em.capacity, em.wrap, slot0 + r, k));
     }
 }
 
@@ -1297,6 +1245,10 @@ constexpr int kWarpClasses = 3;
 constexpr int kCtaClasses = 6;
 constexpr size_t kSmemPerBlock = 96 * 1024;
 
+// Arena slices (resident CTAs) per SM of the CTA form: small subproblems
+// (listing mode's small classes) run four CTAs of 128 threads per SM.
+uint32_t cta_slices_per_sm(uint32_t D) { return D <= 128 ? 4u : 2u; }
+
 size_t cta_smem_bytes(uint32_t D) { return D <= 128 ? 48 * 1024 : D <= 256 ? 100 * 1024 : 200 * 1024; }
 int cta_threads(uint32_t D) { return D <= 128 ? 128 : 512; }
 
@@ -1334,7 +1286,7 @@ void launch_cta(uint32_t k, uint32_t D, Workspace &w, uint32_t begin, uint32_t e
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, smem) != cudaSuccess)
         (void)cudaGetLastError();
     if (occ < 1) occ = 1;
-    if (occ > 2) occ = 2;  // the arena holds two slices per SM
+    if (occ > (int)cta_slices_per_sm(D)) occ = (int)cta_slices_per_sm(D);  // arena slices per SM
     uint32_t blocks = (uint32_t)num_sms * occ;
     if (blocks > end - begin) blocks = end - begin;
     kern<<<blocks, threads, smem, s>>>(k, D, w.optr, w.oadj, w.key, w.roots, begin, end, queue,
@@ -1368,7 +1320,7 @@ size_t sdegree_arena_words(uint32_t k, int num_sms, uint32_t max_outdeg) {
     size_t need = 0;
     for (int c = 0; c < kNumClasses; c++) {
         if (c > 0 && kClassD[c - 1] >= max_outdeg) break;
-        size_t words = c < kCtaClasses ? (size_t)num_sms * 2 * cta_arena_words(kClassD[c])
+        size_t words = c < kCtaClasses ? (size_t)num_sms * cta_slices_per_sm(kClassD[c]) * cta_arena_words(kClassD[c])
                                        : (size_t)num_sms * 2 * make_slayout(kClassD[c], k).total;
         if (words > need) need = words;
     }
