@@ -1249,7 +1249,10 @@ constexpr size_t kSmemPerBlock = 96 * 1024;
 // (listing mode's small classes) run four CTAs of 128 threads per SM.
 uint32_t cta_slices_per_sm(uint32_t D) { return D <= 128 ? 4u : 2u; }
 
-size_t cta_smem_bytes(uint32_t D) { return D <= 128 ? 48 * 1024 : D <= 256 ? 100 * 1024 : 200 * 1024; }
+// Shared memory per CTA: up to d+ = 512 two CTAs fit on an SM (dense
+// subproblems there take the bit-row form, whose rows are at most 40 KB);
+// the largest class keeps one CTA with room for its rows or lists.
+size_t cta_smem_bytes(uint32_t D) { return D <= 128 ? 48 * 1024 : D <= 512 ? 100 * 1024 : 200 * 1024; }
 int cta_threads(uint32_t D) { return D <= 128 ? 128 : 512; }
 
 template <bool LIST>
