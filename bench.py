@@ -205,6 +205,7 @@ def run_ours(args, rank, world):
         "gpu_launches": launches,
         "clocks": clk,
         "roofline": roof,
+        "roofline_counting": roofline(per_call, args.steps, modes=("count",)),
         "stage_ms": stage_summary(per_call, args.steps),
     }
     g.free()
@@ -244,18 +245,27 @@ def stage_summary(per_call, steps):
     return res
 
 
-def roofline(per_call, steps):
+def roofline(per_call, steps, modes=("count", "list")):
     """The dominant kernel: the single listing launch with the largest device
-    time per step -- one out-degree class of the call family whose listing
-    stage is longest.  Its bound is the integer pipe (AND + POPC per bitmap
-    word for BitCol, one compare per merge element for SDegree); the peak is
-    derived from the SM count and clock.  `achieved` = the oracle's
-    algorithmic work for the roots of that class (tests/golden/rmat20_work.json,
-    split by out-degree) / that launch's CUDA-event time."""
+    time per step -- one out-degree class of the call family (among `modes`)
+    whose listing stage is longest.  Its bound is the integer pipe; the peak
+    is derived from the SM count and clock:
+      counting, BitCol: one AND + POPC per bitmap word, 16 POPC per SM and
+        clock; unit = BitJoin words (Algorithm 6);
+      counting, SDegree: at least one compare per merge element, 64 compares
+        per SM and clock; unit = merge elements (Lemma 2);
+      listing (checksum, no ring): k SplitMix64 rounds per clique, each two
+        64-bit multiplies of three 32-bit IMADs, 64 IMADs per SM and clock;
+        unit = cliques.
+    `achieved` = the oracle's algorithmic work (or clique count) for the roots
+    of that class (tests/golden/rmat20_work.json, split by out-degree) / that
+    launch's CUDA-event time."""
     peaks, src = _peaks()
     work = _load_work()
     fam = {}
     for (k, o, m, c, ms, la, cl) in per_call:
+        if m not in modes:
+            continue
         f = fam.setdefault((k, o, m), {"listing": [], "classes": {}})
         f["listing"].append(ms["listing"])
         for ci, cc in enumerate(cl):
@@ -264,25 +274,27 @@ def roofline(per_call, steps):
     (ci, lo, hi, roots), times = max(f["classes"].items(), key=lambda kv: sum(kv[1]))
     avg_ms = sum(times) / len(times)
     sm_mhz = peaks.get("sm_max_mhz", 2070.0)
-    # integer pipe per SM and clock: 16 POPC (BitCol: one AND + POPC per
-    # bitmap word, POPC-limited) or 64 32-bit compares (SDegree: at least one
-    # compare per merge element), on 152 SMs
-    per_clk = 16 if o == "color" else 64
+    entry = work.get("k=%d %s" % (k, o))
+    if m == "list":
+        per_clk, what, unit = 64.0 / (6 * k), "IMAD/clk / (6 k IMAD per clique)", "Gclique/s"
+        wk = class_work(entry, lo, hi, field="count_by_outdeg")
+    else:
+        per_clk = 16 if o == "color" else 64
+        what = "POPC/clk" if o == "color" else "compares/clk"
+        unit = "Gword/s" if o == "color" else "Gelem/s"
+        wk = class_work(entry, lo, hi)
     peak_gops = 152 * per_clk * sm_mhz * 1e6 / 1e9
-    wk = class_work(work.get("k=%d %s" % (k, o)), lo, hi)
     achieved = (wk / (avg_ms / 1e3) / 1e9) if wk else None
     kern = KERNEL_NAMES.get((o, m, ci), "listing launch of class %d" % ci)
     tr = TRAFFIC.get((k, o, m, ci))
     return {"kernel": "%s (k=%d %s %s, roots with %d <= d+ <= %d)" % (kern, k, o, m, lo, hi),
-            "bound": "alu", "achieved": achieved, "peak": peak_gops,
-            "unit": "Gword/s" if o == "color" else "Gelem/s",
+            "bound": "alu", "achieved": achieved, "peak": peak_gops, "unit": unit,
             "frac": (achieved / peak_gops) if achieved else None,
             "traffic": tr[0] if tr else None,
             "traffic_source": tr[1] if tr else None,
             "work_per_launch": wk, "roots": roots, "avg_ms": avg_ms,
             "listing_stage_ms": sum(f["listing"]) / len(f["listing"]),
-            "peak_source": "derived: 152 SMs x %d %s/clk x %.0f MHz (%s clock)"
-                           % (per_clk, "POPC" if o == "color" else "compares", sm_mhz, src)}
+            "peak_source": "derived: 152 SMs x %s x %.0f MHz (%s clock)" % (what, sm_mhz, src)}
 
 
 # listing kernels of the out-degree classes (count mode), by (ordering, mode,
@@ -300,6 +312,18 @@ KERNEL_NAMES = {
     ("color", "count", 3): "k_bitcol_cta<8,0,0,0>",
     ("color", "count", 4): "k_bitcol_cta<16,0,0,0>",
     ("color", "count", 5): "k_bitcol_cta<16,0,1,0>",
+    ("degree", "list", 0): "k_sdegree_cta<1> (d+ <= 32)",
+    ("degree", "list", 1): "k_sdegree_cta<1> (d+ <= 64)",
+    ("degree", "list", 2): "k_sdegree_cta<1> (d+ <= 128)",
+    ("degree", "list", 3): "k_sdegree_cta<1> (d+ <= 256)",
+    ("degree", "list", 4): "k_sdegree_cta<1> (d+ <= 512)",
+    ("degree", "list", 5): "k_sdegree_cta<1> (d+ <= 1024)",
+    ("color", "list", 0): "k_bitcol_cta<4,1,0,0> (W=1)",
+    ("color", "list", 1): "k_bitcol_cta<4,1,0,0> (W=2)",
+    ("color", "list", 2): "k_bitcol_cta<4,1,0,0> (W=4)",
+    ("color", "list", 3): "k_bitcol_cta<8,1,0,0>",
+    ("color", "list", 4): "k_bitcol_cta<16,1,0,0>",
+    ("color", "list", 5): "k_bitcol_cta<16,1,1,0>",
 }
 
 # DRAM bytes (read + write) per launch of the dominant kernel from one ncu
@@ -309,18 +333,18 @@ KERNEL_NAMES = {
 TRAFFIC = {}
 
 
-def class_work(entry, lo, hi):
+def class_work(entry, lo, hi, field="work_by_outdeg"):
     """Oracle work of the roots with lo <= d+ <= hi, from the power-of-two
     out-degree buckets (bucket b: 2^(b-1) < d+ <= 2^b).  Every class starts
     just above a power of two (or at k-1, below which there are no roots) and
     ends at one (or at the largest out-degree), so each bucket lies in one
     class."""
-    if not entry or "work_by_outdeg" not in entry:
+    if not entry or field not in entry:
         return None
     if lo > 1 and (lo - 1) & (lo - 2) and lo - 1 > 32:
         return None
     total = 0
-    for b, w in entry["work_by_outdeg"].items():
+    for b, w in entry[field].items():
         top = 1 << int(b)
         if top >= lo and (top >> 1) < hi:
             total += w

@@ -8,9 +8,10 @@ oracle's count-only mode gives:
             32-bit word for BitCol (Algorithm 6), merge-join elements
             sum(|C| + d+_v) for SDegree (Algorithm 5, the cost model of
             Lemma 2),
-  work_by_outdeg / roots_by_outdeg -- the same work and the number of expanded
-            roots split by the root's out-degree d+_u in power-of-two buckets:
-            key "b" holds the roots with 2^(b-1) < d+_u <= 2^b.
+  work_by_outdeg / roots_by_outdeg / count_by_outdeg -- the same work, the
+            number of expanded roots and the k-cliques they list, split by
+            the root's out-degree d+_u in power-of-two buckets: key "b" holds
+            the roots with 2^(b-1) < d+_u <= 2^b.
 The roots are split into buckets (and each bucket into interleaved shards)
 so that the oracle runs on every core; the count adds the Pre-List cliques
 (Algorithm 4), which the per-root runs leave out.
@@ -86,7 +87,7 @@ def main():
                 tasks += [(job[0], job[1], b, r[s::ns]) for s in range(ns)]
         tasks.sort(key=lambda t: (-t[0], t[1] == "color", -t[2]))
         acc = {job: {"count": plans[job][0], "work": 0, "counters": {}, "work_by_outdeg": {},
-                     "roots_by_outdeg": {}} for job in jobs}
+                     "roots_by_outdeg": {}, "count_by_outdeg": {}} for job in jobs}
         left = {job: sum(1 for t in tasks if (t[0], t[1]) == job) for job in jobs}
         for job, b, cnt, work, ctr in pool.imap_unordered(one, tasks):
             a = acc[job]
@@ -98,11 +99,13 @@ def main():
             key = str(b)
             a["work_by_outdeg"][key] = a["work_by_outdeg"].get(key, 0) + work
             a["roots_by_outdeg"][key] = a["roots_by_outdeg"].get(key, 0) + ctr["roots"]
+            a["count_by_outdeg"][key] = a["count_by_outdeg"].get(key, 0) + cnt
             left[job] -= 1
             if left[job] == 0:
                 a["oracle_wall_seconds"] = round(time.time() - t0, 1)
                 a["work_by_outdeg"] = dict(sorted(a["work_by_outdeg"].items(), key=lambda x: int(x[0])))
                 a["roots_by_outdeg"] = dict(sorted(a["roots_by_outdeg"].items(), key=lambda x: int(x[0])))
+                a["count_by_outdeg"] = dict(sorted(a["count_by_outdeg"].items(), key=lambda x: int(x[0])))
                 data["k=%d %s" % job] = a
                 print("k=%d %s" % job, a, flush=True)
                 with open(OUT, "w") as f:

@@ -48,6 +48,20 @@ def test_roofline_picks_the_longest_launch(monkeypatch):
     assert abs(r["peak"] / rc["peak"] - 4.0) < 1e-12
 
 
+def test_roofline_listing_counts_cliques(monkeypatch):
+    work = {"k=4 color": {"work": 50, "work_by_outdeg": {"5": 50},
+                          "count_by_outdeg": {"5": 7000, "9": 9000}}}
+    monkeypatch.setattr(bench, "_load_work", lambda: work)
+    calls = [_call(4, "color", "list", 40.0, [(3, 32, 10, 10.0), (257, 512, 3, 30.0)]),
+             _call(4, "color", "count", 5.0, [(3, 32, 10, 5.0)])]
+    r = bench.roofline(calls, 1)
+    assert r["unit"] == "Gclique/s" and r["work_per_launch"] == 9000
+    # k SplitMix64 rounds per clique at 6 IMADs each, 64 IMADs per SM and clock
+    assert abs(r["peak"] - 152 * 64 / 24 * 2070e6 / 1e9) < 1e-6
+    rc = bench.roofline(calls, 1, modes=("count",))
+    assert rc["unit"] == "Gword/s" and rc["work_per_launch"] == 50
+
+
 def _free_port():
     with socket.socket() as s:
         s.bind(("127.0.0.1", 0))
