@@ -276,11 +276,11 @@ def roofline(per_call, steps, modes=("count", "list")):
     sm_mhz = peaks.get("sm_max_mhz", 2070.0)
     entry = work.get("k=%d %s" % (k, o))
     if m == "list":
-        per_clk, what, unit = 64.0 / (6 * k), "IMAD/clk / (6 k IMAD per clique)", "Gclique/s"
+        per_clk, what, unit = 64.0 / (6 * k), "64 IMAD/clk / (6 k IMAD per clique)", "Gclique/s"
         wk = class_work(entry, lo, hi, field="count_by_outdeg")
     else:
         per_clk = 16 if o == "color" else 64
-        what = "POPC/clk" if o == "color" else "compares/clk"
+        what = "16 POPC/clk" if o == "color" else "64 compares/clk"
         unit = "Gword/s" if o == "color" else "Gelem/s"
         wk = class_work(entry, lo, hi)
     peak_gops = 152 * per_clk * sm_mhz * 1e6 / 1e9

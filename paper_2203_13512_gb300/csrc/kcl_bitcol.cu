@@ -366,43 +366,59 @@ __device__ void leaf_batch(const View &v, const uint32_t *C, uint32_t cw, const 
     }
     cnt += x;
     if (!LIST) return;
-    // the tot cliques of the batch are enumerated by all lanes together:
-    // clique r belongs to the lane o whose exclusive prefix holds it, and is
-    // the (r - excl_o)-th set bit of B'(q[o]) & C -- hashing is spread evenly
+    // the tot cliques of the batch, in (candidate, bit) order, are cut into
+    // 32 contiguous runs, one per lane: a lane finds its first clique once
+    // (the candidate whose prefix holds it, then its bit) and walks the set
+    // bits of B'(q[o]) & C from there, moving on to the next candidates
     const uint32_t incl = warp_incl_scan(x);
     const uint32_t excl = incl - x;
     const uint32_t tot = __shfl_sync(kFull, incl, 31);
+    if (!tot) return;
     unsigned long long slot0 = 0;
-    if (tot && em.ring) {
+    if (em.ring) {
         if (lane == 0) slot0 = atomicAdd(&res->emitted, (unsigned long long)tot);
         slot0 = __shfl_sync(kFull, slot0, 0);
     }
-    const uint64_t seed = hash_seed(v.k);
-    for (uint32_t base = 0; base < tot; base += 32) {
-        const uint32_t r = base + lane;
-        uint32_t o = 0;  // number of lanes whose inclusive prefix is <= r
+    const uint32_t run = (tot + 31) >> 5;
+    const uint32_t r0 = lane * run;
+    uint32_t o = 0;  // number of lanes whose inclusive prefix is <= r0
 #pragma unroll
-        for (uint32_t step = 16; step > 0; step >>= 1) {
-            const uint32_t vv = __shfl_sync(kFull, incl, o + step - 1);
-            if (vv <= r) o += step;
-        }
-        const uint32_t eo = __shfl_sync(kFull, excl, o & 31u);
-        if (r >= tot) continue;
-        const uint32_t po = q[o];
-        const uint32_t *row = v.B + po * v.WP;
-        const uint32_t wl = row_words(v, po, cw);
-        uint32_t rank = r - eo, qq = 0;
-        for (uint32_t t = 0; t < wl; t++) {
-            const uint32_t mm = row[t] & C[t];
-            const uint32_t c = __popc(mm);
-            if (rank < c) {
-                qq = t * 32 + __fns(mm, 0, (int)rank + 1);
-                break;
-            }
-            rank -= c;
-        }
-        cks += clique_hash2(sortedR, v.k - 2, v.ids[po], v.ids[qq], seed,
+    for (uint32_t step = 16; step > 0; step >>= 1) {
+        const uint32_t vv = __shfl_sync(kFull, incl, o + step - 1);
+        if (vv <= r0) o += step;
+    }
+    const uint32_t eo = __shfl_sync(kFull, excl, o & 31u);
+    if (r0 >= tot) return;
+    const uint32_t r1 = r0 + run < tot ? r0 + run : tot;
+    const uint64_t seed = hash_seed(v.k);
+    uint32_t po = q[o];
+    const uint32_t *row = v.B + po * v.WP;
+    uint32_t wl = row_words(v, po, cw), a = v.ids[po];
+    // the (r0 - eo)-th set bit of the owner's row & C
+    uint32_t rank = r0 - eo, t = 0, mm = 0;
+    for (; t < wl; t++) {
+        mm = row[t] & C[t];
+        const uint32_t c = __popc(mm);
+        if (rank < c) break;
+        rank -= c;
+    }
+    for (uint32_t z = 0; z < rank; z++) mm &= mm - 1;
+    for (uint32_t r = r0; r < r1; r++) {
+        // mm holds the remaining bits of word t (its lowest is clique r)
+        const uint32_t b = t * 32 + (__ffs(mm) - 1);
+        cks += clique_hash2(sortedR, v.k - 2, a, v.ids[b], seed,
                             ring_slot(em.ring, em.capacity, em.wrap, slot0 + r, v.k));
+        mm &= mm - 1;
+        while (!mm && r + 1 < r1) {
+            if (++t >= wl) {  // next candidate with cliques
+                po = q[++o];
+                row = v.B + po * v.WP;
+                wl = row_words(v, po, cw);
+                a = v.ids[po];
+                t = 0;
+            }
+            mm = row[t] & C[t];
+        }
     }
 }
 

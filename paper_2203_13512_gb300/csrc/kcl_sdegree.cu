@@ -742,42 +742,56 @@ __device__ void bleaf_batch(const BView &v, const uint32_t *C, const uint16_t *q
     uint32_t x = lane < nb ? brow_and(v, q[lane], C) : 0u;
     cnt += x;
     if (!LIST) return;
-    // clique r of the batch: the lane o whose prefix holds it, and the
-    // (r - excl_o)-th set bit of row(q[o]) & C
+    // the tot cliques of the batch, in (candidate, bit) order, are cut into
+    // 32 contiguous runs, one per lane; a lane finds its first clique once
+    // and walks the set bits from there (as in BitCol's leaf)
     const uint32_t incl = warp_incl_scan(x);
     const uint32_t excl = incl - x;
     const uint32_t tot = __shfl_sync(kFull, incl, 31);
+    if (!tot) return;
     unsigned long long slot0 = 0;
-    if (tot && em.ring) {
+    if (em.ring) {
         if (lane == 0) slot0 = atomicAdd(&res->emitted, (unsigned long long)tot);
         slot0 = __shfl_sync(kFull, slot0, 0);
     }
+    const uint32_t run = (tot + 31) >> 5;
+    const uint32_t r0 = lane * run;
+    uint32_t o = 0;
+#pragma unroll
+    for (uint32_t step = 16; step > 0; step >>= 1) {
+        const uint32_t vv = __shfl_sync(kFull, incl, o + step - 1);
+        if (vv <= r0) o += step;
+    }
+    const uint32_t eo = __shfl_sync(kFull, excl, o & 31u);
+    if (r0 >= tot) return;
+    const uint32_t r1 = r0 + run < tot ? r0 + run : tot;
     const uint32_t k = v.k;
     const uint64_t seed = hash_seed(k);
-    for (uint32_t base = 0; base < tot; base += 32) {
-        const uint32_t r = base + lane;
-        uint32_t o = 0;
-#pragma unroll
-        for (uint32_t step = 16; step > 0; step >>= 1) {
-            const uint32_t vv = __shfl_sync(kFull, incl, o + step - 1);
-            if (vv <= r) o += step;
-        }
-        const uint32_t eo = __shfl_sync(kFull, excl, o & 31u);
-        if (r >= tot) continue;
-        const uint32_t qo = q[o];
-        const uint32_t *row = v.R + qo * v.WP;
-        uint32_t rank = r - eo, t2 = 0;
-        for (uint32_t t = qo >> 5; t < v.W; t++) {
-            const uint32_t mm = row[t] & C[t];
-            const uint32_t c = __popc(mm);
-            if (rank < c) {
-                t2 = t * 32 + __fns(mm, 0, (int)rank + 1);
-                break;
-            }
-            rank -= c;
-        }
-        cks += clique_hash2(sortedR, k - 2, v.ids[qo], v.ids[t2], seed,
+    uint32_t qo = q[o];
+    const uint32_t *row = v.R + qo * v.WP;
+    uint32_t a = v.ids[qo];
+    uint32_t rank = r0 - eo, t = qo >> 5, mm = 0;
+    for (; t < v.W; t++) {
+        mm = row[t] & C[t];
+        const uint32_t c = __popc(mm);
+        if (rank < c) break;
+        rank -= c;
+    }
+    for (uint32_t z = 0; z < rank; z++) mm &= mm - 1;
+    for (uint32_t r = r0; r < r1; r++) {
+        const uint32_t b = t * 32 + (__ffs(mm) - 1);
+        cks += clique_hash2(sortedR, k - 2, a, v.ids[b], seed,
                             ring_slot(em.ring, em.capacity, em.wrap, slot0 + r, k));
+        mm &= mm - 1;
+        while (!mm && r + 1 < r1) {
+            if (++t >= v.W) {  // next candidate with cliques
+                qo = q[++o];
+                row = v.R + qo * v.WP;
+                a = v.ids[qo];
+                t = qo >> 5;
+            }
+            mm = row[t] & C[t];
+        }
     }
 }
 
