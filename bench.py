@@ -330,7 +330,15 @@ KERNEL_NAMES = {
 # capture of the same workload, keyed like KERNEL_NAMES plus k; the source names
 # the summary under profiles/.  Empty until a capture of the current kernel
 # exists.
-TRAFFIC = {}
+_DRAM = "profiles/dram_listing_kernels_rmat20.md"
+TRAFFIC = {
+    (5, "degree", "count", 3): (31.54e6, _DRAM),
+    (5, "degree", "count", 5): (14.36e6, _DRAM),
+    (4, "degree", "list", 4): (35.97e6, _DRAM),
+    (4, "degree", "list", 5): (14.48e6, _DRAM),
+    (4, "color", "list", 4): (31.27e6, _DRAM),
+    (4, "color", "list", 5): (13.65e6, _DRAM),
+}
 
 
 def class_work(entry, lo, hi, field="work_by_outdeg"):
