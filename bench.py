@@ -326,10 +326,10 @@ KERNEL_NAMES = {
     ("color", "list", 5): "k_bitcol_cta<16,1,1,0>",
 }
 
-# DRAM bytes (read + write) per launch of the dominant kernel from one ncu
-# capture of the same workload, keyed like KERNEL_NAMES plus k; the source names
-# the summary under profiles/.  Empty until a capture of the current kernel
-# exists.
+# DRAM bytes (read + write) per launch of the listing launches from one ncu
+# capture of the same workload, keyed (k, ordering, mode, class); the source
+# names the summary under profiles/.  An entry is removed when its kernel
+# changes, until a new capture exists.
 _DRAM = "profiles/dram_listing_kernels_rmat20.md"
 TRAFFIC = {
     (5, "degree", "count", 3): (31.54e6, _DRAM),
