@@ -568,20 +568,25 @@ def run_serve(args):
 
 
 def run_ablation(args):
-    """The preprocessing / pruning study and the memory study on the bench
-    graph (R-MAT scale 20): for k = 4, 5 and both orderings, device time of
-    one call with everything on, without Pre-Core, without Pre-List, and
-    (BitCol) without the colour prune; and the device scratch a fresh handle
-    holds after one call of each (k, ordering)."""
+    """The preprocessing / pruning study, the NodeParallel / EdgeParallel study
+    and the memory study on the bench graph (R-MAT scale 20): for k = 4, 5
+    and both orderings, device time of one call with everything on, without
+    Pre-Core, without Pre-List, (BitCol) without the colour prune, and with
+    one warp per root in the CTA classes (NodeParallel: no sharing of a
+    root's first-level children); and the device scratch a fresh handle holds
+    after one call of each (k, ordering)."""
     import torch
 
     import paper_2203_13512_gb300 as kcl
     rp, col = workload()
     g = kcl.kcl_load_csr(rp, col)
     kcl.kcl_enable_timing(g, True)
-    configs = [("all on", 0), ("no Pre-Core", kcl.KCL_OPT_NO_PRECORE),
-               ("no Pre-List", kcl.KCL_OPT_NO_PRELIST),
-               ("no colour prune", kcl.KCL_OPT_NO_COLOR_PRUNE)]
+    one_warp = {"sdegree_cta_warps": [1] * kcl.KCL_MAX_CLASSES,
+                "bitcol_cta_warps": [1] * kcl.KCL_MAX_CLASSES}
+    configs = [("all on", 0, None), ("no Pre-Core", kcl.KCL_OPT_NO_PRECORE, None),
+               ("no Pre-List", kcl.KCL_OPT_NO_PRELIST, None),
+               ("no colour prune", kcl.KCL_OPT_NO_COLOR_PRUNE, None),
+               ("one warp per root (NodeParallel)", 0, one_warp)]
     out = {"metric": "ablation: device ms per call (R-MAT scale 20)", "unit": "ms",
            "higher_is_better": False, "n_gpus": 1,
            "config": {"workload": "rmat-scale20-ef16", "repeats": args.steps},
@@ -589,10 +594,11 @@ def run_ablation(args):
     for k in (4, 5):
         for o in ("color", "degree"):
             row = {}
-            for name, flags in configs:
+            for name, flags, tune in configs:
                 if o == "degree" and flags == kcl.KCL_OPT_NO_COLOR_PRUNE:
                     continue
                 kcl.kcl_set_options(g, flags)
+                kcl.kcl_set_tuning(g, tune or {})
                 c0 = kcl.kcl_count(g, k, o)  # warm-up
                 ms = []
                 for _ in range(max(1, args.steps)):
@@ -609,6 +615,7 @@ def run_ablation(args):
             out["scratch_bytes"]["k=%d %s" % (k, o)] = {"workspace": ws, "arena": ar}
             v.free()
     kcl.kcl_set_options(g, 0)
+    kcl.kcl_set_tuning(g, {})
     g.free()
     return out
 

@@ -259,12 +259,20 @@ kcl_status kcl_scratch_bytes(const kcl_graph *g, uint64_t *workspace, uint64_t *
  *   words), t = sdegree_bitmap[c] (0 means the default t = 16: lists larger
  *   than rows; 0xFFFFFFFF = lists always).  Both forms compute the same
  *   intersections; only their representation differs.
+ * sdegree_cta_warps[c], bitcol_cta_warps[c]: warps per subproblem for the
+ *   CTA-per-root classes of each path: how many of the CTA's warps walk the
+ *   root's first-level
+ *   children (the EdgeParallel units of Section IX-C) after the shared build;
+ *   0 = all of them (default), 1 = one warp walks the whole subtree
+ *   (NodeParallel), k = at most k warps.
  * A graph starts with the defaults; views and batches start with the
  * defaults too. */
 typedef struct {
     uint32_t sdegree_gallop[KCL_MAX_CLASSES];
     uint32_t sdegree_gallop_list[KCL_MAX_CLASSES];
     uint32_t sdegree_bitmap[KCL_MAX_CLASSES];
+    uint32_t sdegree_cta_warps[KCL_MAX_CLASSES];
+    uint32_t bitcol_cta_warps[KCL_MAX_CLASSES];
 } kcl_tuning;
 kcl_status kcl_get_tuning(const kcl_graph *g, kcl_tuning *t);
 kcl_status kcl_set_tuning(kcl_graph *g, const kcl_tuning *t);
@@ -273,7 +281,8 @@ kcl_status kcl_set_tuning(kcl_graph *g, const kcl_tuning *t);
  * launch with CUDA events, and keeps for each class the fastest setting (a
  * later candidate must be 2% faster).  For KCL_ORDER_DEGREE it tunes
  * sdegree_bitmap first (candidates 0, 4, 64, 0xFFFFFFFF), then that mode's
- * galloping array (0, 40, 80, 160, 400); BitCol has no knob yet.  The tuning
+ * galloping array (0, 40, 80, 160, 400); for both orderings it then tunes
+ * that path's cta_warps array (0, 4, 8).  The tuning
  * is stored in g and copied to *out when out is not NULL.  Timing stays as
  * the caller left it.  Errors: those of kcl_count / kcl_list. */
 kcl_status kcl_autotune(kcl_graph *g, uint32_t k, kcl_ordering ord, int listing, kcl_tuning *out);

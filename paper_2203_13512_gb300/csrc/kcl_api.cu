@@ -846,6 +846,11 @@ kcl_status kcl_autotune(kcl_graph *g, uint32_t k, kcl_ordering ord, int listing,
                            listing ? g->tuning.sdegree_gallop_list : g->tuning.sdegree_gallop,
                            gallop_cand, 5);
     }
+    static const uint32_t warps_cand[] = {0, 4, 8};
+    if (st == KCL_OK)
+        st = tune_knob(g, k, ord, listing,
+                       ord == KCL_ORDER_DEGREE ? g->tuning.sdegree_cta_warps : g->tuning.bitcol_cta_warps,
+                       warps_cand, 3);
     if (!was_enabled) kcl_enable_timing(g, 0);
     if (st != KCL_OK) return st;
     if (out) *out = g->tuning;

@@ -301,6 +301,7 @@ struct Emit {
     unsigned long long *root_cks;  // listing: per-root checksum sums, or null
     const uint32_t *idmap;         // listing: vertex -> output id, or null (identity)
     uint32_t prune;                // 1: Lemma 1 colour prune (0 only for ablations)
+    uint32_t dfs_warps;            // CTA form: warps walking the children (0 = all)
 };
 
 struct View {  // read-only view of a built subproblem, per warp
@@ -658,6 +659,9 @@ __global__ void __launch_bounds__(NW * 32) k_bitcol_cta(uint32_t k, uint32_t W,
     __shared__ uint32_t root_idx;
     const unsigned lane = lane_id();
     const uint32_t warp = threadIdx.x >> 5;
+    // warps that walk the root's children: all of them (EdgeParallel units
+    // shared out) unless the tuning caps it (1 = one warp per root)
+    const uint32_t nd = em.dfs_warps && em.dfs_warps < (blockDim.x >> 5) ? em.dfs_warps : (blockDim.x >> 5);
     const SubLay L = sub_layout(W, AG, BG);
     const size_t rows_a = (size_t)L.D * L.WP, rows_b = (size_t)L.D * L.WPB;
     uint32_t *slice = arena + (size_t)blockIdx.x * ((AG ? rows_a : 0) + (BG ? rows_b : 0));
@@ -689,10 +693,10 @@ __global__ void __launch_bounds__(NW * 32) k_bitcol_cta(uint32_t k, uint32_t W,
                 stack[t] = t < dw ? (t * 32 + 32 <= d ? kFull : (1u << (d - t * 32)) - 1u) : 0u;
             __syncwarp();
             uint32_t *path = stack + 2 * k * W, *sortedR = path + 2 * k;
-            leaf<LIST>(v, stack, dw, 0, warp, blockDim.x >> 5, path, sortedR, em, res, cnt, cks);
+            if (warp < nd) leaf<LIST>(v, stack, dw, 0, warp, nd, path, sortedR, em, res, cnt, cks);
         } else {
             const uint32_t nch = root_children<NW>(v, s);
-            for (;;) {
+            for (; warp < nd;) {
                 uint32_t i = 0;
                 if (lane == 0) i = atomicAdd(&s.meta[2], 1u);
                 i = __shfl_sync(kFull, i, 0);
@@ -817,7 +821,7 @@ int launch_bitcol(const kcl_graph *g, uint32_t k, Workspace &w, const uint32_t *
                   int n_classes, const ListArgs &la, cudaStream_t s) {
     // class c covers root positions [class_begin[c], c ? class_begin[c-1] : n_roots)
     Emit em{la.ring, la.capacity, la.wrap, la.per_root_cks, la.idmap,
-            (g->options & KCL_OPT_NO_COLOR_PRUNE) ? 0u : 1u};
+            (g->options & KCL_OPT_NO_COLOR_PRUNE) ? 0u : 1u, 0u};
     int launches = 0;
     cudaMemsetAsync(w.queue, 0, 64 * sizeof(unsigned), s);
     for (int c = 0; c < n_classes; c++) {
@@ -826,6 +830,7 @@ int launch_bitcol(const kcl_graph *g, uint32_t k, Workspace &w, const uint32_t *
         if (end <= begin) continue;
         const ClassCfg &cc = kClass[c];
         unsigned *q = w.queue + c;
+        em.dfs_warps = g->tuning.bitcol_cta_warps[c];
         const size_t smem = class_smem(c, k);
         class_mark(la, c, 0, s);
         if (!cc.cta && la.listing) {

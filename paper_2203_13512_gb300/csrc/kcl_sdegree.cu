@@ -555,151 +555,6 @@ __device__ void ldfs_child(const LView &v, uint32_t p0, const LStack &st, const 
 
 // Warp per root (d+ <= 128): bit-row build in shared memory, padded lists,
 // then the root's children in turn.
-// Rank of member i of N+_u (ascending ids nbr[]) in the DAG order (key, id):
-// members with a smaller key, plus earlier members with the same key.
-__device__ __forceinline__ uint32_t dag_rank(const uint32_t *keys, uint32_t d, uint32_t i) {
-    const uint32_t ki = keys[i];
-    uint32_t r = 0;
-    for (uint32_t j = 0; j < d; j++) {
-        const uint32_t kj = keys[j];
-        r += (kj < ki) | ((kj == ki) & (j < i));
-    }
-    return r;
-}
-
-template <bool LIST>
-__device__ void sdegree_root_local(uint32_t u, uint32_t k, uint32_t D, const uint32_t *__restrict__ optr,
-                                   const uint32_t *__restrict__ oadj, const uint32_t *__restrict__ key,
-                                   uint32_t *S, const Emit &em, DevResult *res, uint32_t gallop,
-                                   unsigned long long &cnt, unsigned long long &cks) {
-    const LLay L = make_llayout(D, k, LIST);
-    const unsigned lane = lane_id();
-    uint32_t *nbr = S + L.NBR;
-    uint32_t *lofs = S + L.LOFS;
-    uint32_t *pre = S + L.PRE;
-    uint32_t *rs = S + L.RS;
-    uint32_t *hk = S + L.HK;
-    uint16_t *hv = reinterpret_cast<uint16_t *>(S + L.HV);
-    uint16_t *len = reinterpret_cast<uint16_t *>(S + L.LEN);
-    uint16_t *rk = reinterpret_cast<uint16_t *>(S + L.RK);
-    uint32_t *bits = S + L.BITS;
-    uint16_t *ladj = reinterpret_cast<uint16_t *>(S + L.LADJ);
-    const LStack st = stack_ptrs(S + L.STACK, D, k, LIST);
-
-    const uint32_t base = optr[u];
-    const uint32_t d = optr[u + 1] - base;
-    uint32_t running = 0;
-    for (uint32_t c0 = 0; c0 < d; c0 += 32) {
-        uint32_t i = c0 + lane, x = 0;
-        if (i < d) {
-            uint32_t v = oadj[base + i];
-            nbr[i] = v;
-            uint32_t r0 = optr[v];
-            rs[i] = r0;
-            x = optr[v + 1] - r0;
-            lofs[i] = key[v];  // keys until the list offsets are laid out
-        }
-        uint32_t incl = x;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            uint32_t y = __shfl_up_sync(kFull, incl, o);
-            if (lane >= (unsigned)o) incl += y;
-        }
-        if (i < d) pre[i] = running + incl - x;
-        running += __shfl_sync(kFull, incl, 31);
-    }
-    for (uint32_t i = lane; i < d * L.WPD; i += 32) bits[i] = 0;
-    if (lane == 0) pre[d] = running;
-    __syncwarp();
-    const uint32_t total = running;
-    const uint32_t lo_id = nbr[0], hi_id = nbr[d - 1];
-    // local index = rank in the DAG order, so every reduced out-list L(i)
-    // holds only indices above i
-    for (uint32_t i = lane; i < d; i += 32) rk[i] = (uint16_t)dag_rank(lofs, d, i);
-    __syncwarp();
-
-    // directed bit-rows: the members' out-lists are streamed as one flattened
-    // sequence; a hash probe into N+_u finds the local index of each entry
-    uint32_t T, hshift;
-    hash_size(d, &T, &hshift);
-    warp_hash_build(nbr, d, hk, hv, T, hshift);
-    uint32_t a0 = 0;
-    for (uint32_t c = 0; c < total; c += 32) {
-        const uint32_t e = c + lane;
-        uint32_t a = a0;
-        if (e < total) {
-            while (pre[a + 1] <= e) a++;
-            uint32_t x = oadj[rs[a] + (e - pre[a])];
-            if (x >= lo_id && x <= hi_id) {
-                int j = hash_find(hk, hv, T, hshift, x);
-                if (j >= 0) {
-                    const uint32_t jr = rk[j];
-                    atomicOr(&bits[rk[a] * L.WPD + (jr >> 5)], 1u << (jr & 31));
-                }
-            }
-        }
-        a0 = __shfl_sync(kFull, a, 31);
-    }
-    __syncwarp();
-    // member ids by local index (rs is free after the build)
-    for (uint32_t i = lane; i < d; i += 32) rs[rk[i]] = nbr[i];
-    __syncwarp();
-    // lengths -> padded offsets -> lists in ascending order
-    running = 0;
-    for (uint32_t c0 = 0; c0 <= d; c0 += 32) {
-        uint32_t i = c0 + lane, x = 0;
-        if (i < d) {
-            uint32_t c = 0;
-            for (uint32_t t = 0; t < L.WPD; t++) c += __popc(bits[i * L.WPD + t]);
-            len[i] = (uint16_t)c;
-            x = round4(c);
-        }
-        uint32_t incl = x;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            uint32_t y = __shfl_up_sync(kFull, incl, o);
-            if (lane >= (unsigned)o) incl += y;
-        }
-        if (i <= d) lofs[i] = running + incl - x;
-        running += __shfl_sync(kFull, incl, 31);
-    }
-    __syncwarp();
-    for (uint32_t i = lane; i < d; i += 32) {
-        uint32_t o = lofs[i];
-        for (uint32_t t = 0; t < L.WPD; t++) {
-            uint32_t m = bits[i * L.WPD + t];
-            while (m) {
-                ladj[o++] = (uint16_t)(t * 32 + (__ffs(m) - 1));
-                m &= m - 1;
-            }
-        }
-        while (o < lofs[i + 1]) ladj[o++] = kPad;
-    }
-    __syncwarp();
-
-    if (LIST && em.idmap) {  // output ids (batched unions map back to each graph's ids)
-        for (uint32_t i = lane; i < d; i += 32) rs[i] = em.idmap[rs[i]];
-        __syncwarp();
-    }
-    const LView v{rs, lofs, len, ladj, d, (LIST && em.idmap) ? em.idmap[u] : u, k, gallop};
-    if (k == 3) {
-        // C = all of N+_u: every edge of the reduced DAG closes a triangle
-        if (!LIST) {
-            uint32_t c = 0;
-            for (uint32_t i = lane; i < d; i += 32) c += len[i];
-            cnt += c;
-            return;
-        }
-        for (uint32_t i = lane; i < round4(d); i += 32) st.clist[i] = i < d ? (uint16_t)i : kPad;
-        __syncwarp();
-        lleaf<LIST>(v, st.clist, d, 0, d, 0, st, em, res, cnt, cks);
-        return;
-    }
-    // depth 0: C = all local indices, so |L(w) intersect C| = |L(w)|
-    for (uint32_t w = 0; w < d; w++)
-        if (v.deg(w) + 2 >= k) ldfs_child<LIST>(v, w, st, em, res, cnt, cks);
-}
-
 // ------------------------------------- bit-row form of SDegreeList
 // For dense subproblems the reduced out-lists take more room than the
 // directed bit-rows of the same DAG (16 bits per edge against 1 bit per
@@ -710,9 +565,9 @@ __device__ void sdegree_root_local(uint32_t u, uint32_t k, uint32_t D, const uin
 // indices follow the DAG order, so row(v) holds only indices above v and the
 // AND for candidate v starts at v's 4-word chunk.
 struct BView {
-    const uint32_t *R;    // bit-rows, stride WP words (16-byte aligned rows)
+    const uint32_t *R;    // bit-rows, stride WP words
     const uint32_t *ids;  // local index -> output id
-    uint32_t d, W, WP, u, k;  // W: words per row, a multiple of 4
+    uint32_t d, W, WP, u, k;  // W: words per row
 };
 
 __host__ __device__ inline uint32_t bstack_words(uint32_t W, uint32_t k) {
@@ -720,14 +575,21 @@ __host__ __device__ inline uint32_t bstack_words(uint32_t W, uint32_t k) {
     return (k * (2 * W + 2) + 64 + 3) & ~3u;
 }
 
-// |row(q) & C|; C is zero beyond its W words and row(q) below q's chunk
+// |row(q) & C|; C is zero beyond its W words and row(q) below q's word.
+// Rows of a multiple of 4 words on a 16-byte stride are read as 128-bit
+// vectors from q's chunk on; narrow rows (the warp form) word by word.
 __device__ __forceinline__ uint32_t brow_and(const BView &v, uint32_t q, const uint32_t *C) {
-    const uint4 *r4 = reinterpret_cast<const uint4 *>(v.R + q * v.WP);
-    const uint4 *c4 = reinterpret_cast<const uint4 *>(C);
     uint32_t x = 0;
-    for (uint32_t t = q >> 7; t < (v.W >> 2); t++) {
-        const uint4 a = r4[t], b = c4[t];
-        x += __popc(a.x & b.x) + __popc(a.y & b.y) + __popc(a.z & b.z) + __popc(a.w & b.w);
+    if (((v.W | v.WP) & 3u) == 0) {
+        const uint4 *r4 = reinterpret_cast<const uint4 *>(v.R + q * v.WP);
+        const uint4 *c4 = reinterpret_cast<const uint4 *>(C);
+        for (uint32_t t = q >> 7; t < (v.W >> 2); t++) {
+            const uint4 a = r4[t], b = c4[t];
+            x += __popc(a.x & b.x) + __popc(a.y & b.y) + __popc(a.z & b.z) + __popc(a.w & b.w);
+        }
+    } else {
+        const uint32_t *row = v.R + q * v.WP;
+        for (uint32_t t = q >> 5; t < v.W; t++) x += __popc(row[t] & C[t]);
     }
     return x;
 }
@@ -896,6 +758,162 @@ __device__ void bdfs_child(const BView &v, uint32_t p0, uint32_t *stack, const E
     }
 }
 
+// Rank of member i of N+_u (ascending ids nbr[]) in the DAG order (key, id):
+// members with a smaller key, plus earlier members with the same key.
+__device__ __forceinline__ uint32_t dag_rank(const uint32_t *keys, uint32_t d, uint32_t i) {
+    const uint32_t ki = keys[i];
+    uint32_t r = 0;
+    for (uint32_t j = 0; j < d; j++) {
+        const uint32_t kj = keys[j];
+        r += (kj < ki) | ((kj == ki) & (j < i));
+    }
+    return r;
+}
+
+template <bool LIST>
+__device__ void sdegree_root_local(uint32_t u, uint32_t k, uint32_t D, const uint32_t *__restrict__ optr,
+                                   const uint32_t *__restrict__ oadj, const uint32_t *__restrict__ key,
+                                   uint32_t *S, const Emit &em, DevResult *res, uint32_t gallop,
+                                   uint32_t bitmap, unsigned long long &cnt, unsigned long long &cks) {
+    const LLay L = make_llayout(D, k, LIST);
+    const unsigned lane = lane_id();
+    uint32_t *nbr = S + L.NBR;
+    uint32_t *lofs = S + L.LOFS;
+    uint32_t *pre = S + L.PRE;
+    uint32_t *rs = S + L.RS;
+    uint32_t *hk = S + L.HK;
+    uint16_t *hv = reinterpret_cast<uint16_t *>(S + L.HV);
+    uint16_t *len = reinterpret_cast<uint16_t *>(S + L.LEN);
+    uint16_t *rk = reinterpret_cast<uint16_t *>(S + L.RK);
+    uint32_t *bits = S + L.BITS;
+    uint16_t *ladj = reinterpret_cast<uint16_t *>(S + L.LADJ);
+    const LStack st = stack_ptrs(S + L.STACK, D, k, LIST);
+
+    const uint32_t base = optr[u];
+    const uint32_t d = optr[u + 1] - base;
+    uint32_t running = 0;
+    for (uint32_t c0 = 0; c0 < d; c0 += 32) {
+        uint32_t i = c0 + lane, x = 0;
+        if (i < d) {
+            uint32_t v = oadj[base + i];
+            nbr[i] = v;
+            uint32_t r0 = optr[v];
+            rs[i] = r0;
+            x = optr[v + 1] - r0;
+            lofs[i] = key[v];  // keys until the list offsets are laid out
+        }
+        uint32_t incl = x;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(kFull, incl, o);
+            if (lane >= (unsigned)o) incl += y;
+        }
+        if (i < d) pre[i] = running + incl - x;
+        running += __shfl_sync(kFull, incl, 31);
+    }
+    for (uint32_t i = lane; i < d * L.WPD; i += 32) bits[i] = 0;
+    if (lane == 0) pre[d] = running;
+    __syncwarp();
+    const uint32_t total = running;
+    const uint32_t lo_id = nbr[0], hi_id = nbr[d - 1];
+    // local index = rank in the DAG order, so every reduced out-list L(i)
+    // holds only indices above i
+    for (uint32_t i = lane; i < d; i += 32) rk[i] = (uint16_t)dag_rank(lofs, d, i);
+    __syncwarp();
+
+    // directed bit-rows: the members' out-lists are streamed as one flattened
+    // sequence; a hash probe into N+_u finds the local index of each entry
+    uint32_t T, hshift;
+    hash_size(d, &T, &hshift);
+    warp_hash_build(nbr, d, hk, hv, T, hshift);
+    uint32_t a0 = 0;
+    for (uint32_t c = 0; c < total; c += 32) {
+        const uint32_t e = c + lane;
+        uint32_t a = a0;
+        if (e < total) {
+            while (pre[a + 1] <= e) a++;
+            uint32_t x = oadj[rs[a] + (e - pre[a])];
+            if (x >= lo_id && x <= hi_id) {
+                int j = hash_find(hk, hv, T, hshift, x);
+                if (j >= 0) {
+                    const uint32_t jr = rk[j];
+                    atomicOr(&bits[rk[a] * L.WPD + (jr >> 5)], 1u << (jr & 31));
+                }
+            }
+        }
+        a0 = __shfl_sync(kFull, a, 31);
+    }
+    __syncwarp();
+    // member ids by local index (rs is free after the build)
+    for (uint32_t i = lane; i < d; i += 32) rs[rk[i]] = nbr[i];
+    __syncwarp();
+    // lengths -> padded offsets -> lists in ascending order
+    running = 0;
+    for (uint32_t c0 = 0; c0 <= d; c0 += 32) {
+        uint32_t i = c0 + lane, x = 0;
+        if (i < d) {
+            uint32_t c = 0;
+            for (uint32_t t = 0; t < L.WPD; t++) c += __popc(bits[i * L.WPD + t]);
+            len[i] = (uint16_t)c;
+            x = round4(c);
+        }
+        uint32_t incl = x;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(kFull, incl, o);
+            if (lane >= (unsigned)o) incl += y;
+        }
+        if (i <= d) lofs[i] = running + incl - x;
+        running += __shfl_sync(kFull, incl, 31);
+    }
+    __syncwarp();
+    // bit-row form when the lists would take more than threshold/16 of the
+    // rows' room (the rows are already built, in shared memory)
+    const uint32_t thr = bitmap ? bitmap : 16u;
+    const bool bitrows = k > 3 && bitmap != 0xFFFFFFFFu &&
+                         16ull * (lofs[d] / 2) > (unsigned long long)thr * (d * L.WPD);
+    for (uint32_t i = bitrows ? d : lane; i < d; i += 32) {
+        uint32_t o = lofs[i];
+        for (uint32_t t = 0; t < L.WPD; t++) {
+            uint32_t m = bits[i * L.WPD + t];
+            while (m) {
+                ladj[o++] = (uint16_t)(t * 32 + (__ffs(m) - 1));
+                m &= m - 1;
+            }
+        }
+        while (o < lofs[i + 1]) ladj[o++] = kPad;
+    }
+    __syncwarp();
+
+    if (LIST && em.idmap) {  // output ids (batched unions map back to each graph's ids)
+        for (uint32_t i = lane; i < d; i += 32) rs[i] = em.idmap[rs[i]];
+        __syncwarp();
+    }
+    const LView v{rs, lofs, len, ladj, d, (LIST && em.idmap) ? em.idmap[u] : u, k, gallop};
+    if (bitrows) {
+        const BView bv{bits, rs, d, (d + 31) >> 5, L.WPD, v.u, k};
+        for (uint32_t w = 0; w < d; w++)
+            if (v.deg(w) + 2 >= k) bdfs_child<LIST>(bv, w, S + L.STACK, em, res, cnt, cks);
+        return;
+    }
+    if (k == 3) {
+        // C = all of N+_u: every edge of the reduced DAG closes a triangle
+        if (!LIST) {
+            uint32_t c = 0;
+            for (uint32_t i = lane; i < d; i += 32) c += len[i];
+            cnt += c;
+            return;
+        }
+        for (uint32_t i = lane; i < round4(d); i += 32) st.clist[i] = i < d ? (uint16_t)i : kPad;
+        __syncwarp();
+        lleaf<LIST>(v, st.clist, d, 0, d, 0, st, em, res, cnt, cks);
+        return;
+    }
+    // depth 0: C = all local indices, so |L(w) intersect C| = |L(w)|
+    for (uint32_t w = 0; w < d; w++)
+        if (v.deg(w) + 2 >= k) ldfs_child<LIST>(v, w, st, em, res, cnt, cks);
+}
+
 // ------------------------------------------------ CTA per root (d+ > 128)
 // Shared region (words) of the CTA form; the reduced lists and the per-warp
 // stacks follow it in shared memory (lists move to the global arena when
@@ -938,8 +956,8 @@ __global__ void __launch_bounds__(512) k_sdegree_cta(uint32_t k, uint32_t D, con
                                                     const uint32_t *__restrict__ roots, uint32_t begin,
                                                     uint32_t end, unsigned *queue, uint32_t *arena,
                                                     uint32_t smem_words, Emit em, uint32_t gallop,
-                                                    uint32_t bitmap, unsigned long long *per_root,
-                                                    DevResult *res) {
+                                                    uint32_t bitmap, uint32_t dfs_warps,
+                                                    unsigned long long *per_root, DevResult *res) {
     extern __shared__ uint32_t smem[];
     const CLay L = make_clayout(D);
     const uint32_t tid = threadIdx.x, nth = blockDim.x, lane = lane_id(), warp = tid >> 5;
@@ -1116,7 +1134,10 @@ __global__ void __launch_bounds__(512) k_sdegree_cta(uint32_t k, uint32_t D, con
             }
             while (o < lofs[i + 1]) ladj[o++] = kPad;
         }
-        const uint32_t nw_dfs = meta[5], sw = meta[6];
+        // warps walking the children: as many as fit, unless the tuning caps
+        // it (1 = one warp per root)
+        const uint32_t nw_dfs = dfs_warps && dfs_warps < meta[5] ? dfs_warps : meta[5];
+        const uint32_t sw = meta[6];
         if (nw_dfs == 0 && tid == 0) atomicOr(&res->status, DEV_ERR_INTERNAL);  // no stack fits
         if (LIST && em.idmap)  // output ids (batched unions map back to each graph's ids)
             for (uint32_t i = tid; i < d; i += nth) rs[i] = em.idmap[rs[i]];
@@ -1211,6 +1232,7 @@ __global__ void __launch_bounds__(128) k_sdegree(uint32_t k, uint32_t D, const u
                                                 const uint32_t *__restrict__ roots, uint32_t begin,
                                                 uint32_t end, unsigned *queue, uint32_t *arena,
                                                 uint32_t words_per_warp, Emit em, uint32_t gallop,
+                                                uint32_t bitmap,
                                                 unsigned long long *per_root, DevResult *res) {
     extern __shared__ uint32_t smem[];
     const unsigned lane = lane_id();
@@ -1226,7 +1248,7 @@ __global__ void __launch_bounds__(128) k_sdegree(uint32_t k, uint32_t D, const u
         uint32_t u = roots[begin + idx];
         unsigned long long before = cnt;
         const unsigned long long before_cks = cks;
-        if (LOCAL) sdegree_root_local<LIST>(u, k, D, optr, oadj, key, S, em, res, gallop, cnt, cks);
+        if (LOCAL) sdegree_root_local<LIST>(u, k, D, optr, oadj, key, S, em, res, gallop, bitmap, cnt, cks);
         else sdegree_root<LIST>(u, k, D, optr, oadj, S, em, res, cnt, cks);
         if (per_root) {
             unsigned long long mine = cnt - before;
@@ -1272,7 +1294,7 @@ int cta_threads(uint32_t D) { return D <= 128 ? 128 : 512; }
 template <bool LIST>
 void launch_warp_local(uint32_t k, uint32_t D, Workspace &w, uint32_t begin, uint32_t end,
                        unsigned *queue, const Emit &em, unsigned long long *per_root, int num_sms,
-                       uint32_t gallop, cudaStream_t s) {
+                       uint32_t gallop, uint32_t bitmap, cudaStream_t s) {
     uint32_t words = make_llayout(D, k, LIST).total;
     int wpb = (int)(kSmemPerBlock / ((size_t)words * 4));
     if (wpb > 4) wpb = 4;
@@ -1288,13 +1310,13 @@ void launch_warp_local(uint32_t k, uint32_t D, Workspace &w, uint32_t begin, uin
     uint32_t need = (end - begin + wpb - 1) / wpb;
     if (blocks > need) blocks = need;
     kern<<<blocks, wpb * 32, smem, s>>>(k, D, w.optr, w.oadj, w.key, w.roots, begin, end, queue,
-                                        w.arena, words, em, gallop, per_root, w.res);
+                                        w.arena, words, em, gallop, bitmap, per_root, w.res);
 }
 
 template <bool LIST>
 void launch_cta(uint32_t k, uint32_t D, Workspace &w, uint32_t begin, uint32_t end, unsigned *queue,
                 const Emit &em, unsigned long long *per_root, int num_sms, uint32_t gallop,
-                uint32_t bitmap, cudaStream_t s) {
+                uint32_t bitmap, uint32_t dfs_warps, cudaStream_t s) {
     size_t smem = cta_smem_bytes(D);
     const int threads = cta_threads(D);
     auto kern = k_sdegree_cta<LIST>;
@@ -1307,8 +1329,8 @@ void launch_cta(uint32_t k, uint32_t D, Workspace &w, uint32_t begin, uint32_t e
     uint32_t blocks = (uint32_t)num_sms * occ;
     if (blocks > end - begin) blocks = end - begin;
     kern<<<blocks, threads, smem, s>>>(k, D, w.optr, w.oadj, w.key, w.roots, begin, end, queue,
-                                       w.arena, (uint32_t)(smem / 4), em, gallop, bitmap, per_root,
-                                       w.res);
+                                       w.arena, (uint32_t)(smem / 4), em, gallop, bitmap, dfs_warps,
+                                       per_root, w.res);
 }
 
 template <bool LIST>
@@ -1319,8 +1341,8 @@ void launch_global_lists(uint32_t k, uint32_t D, Workspace &w, uint32_t begin, u
     uint32_t blocks = (uint32_t)num_sms;
     if (blocks * 2 > end - begin) blocks = (end - begin + 1) / 2;
     k_sdegree<LIST, true, false><<<blocks, 64, 0, s>>>(k, D, w.optr, w.oadj, w.key, w.roots, begin,
-                                                       end, queue, w.arena, words, em, gallop, per_root,
-                                                       w.res);
+                                                       end, queue, w.arena, words, em, gallop, 0u,
+                                                       per_root, w.res);
 }
 
 }  // namespace
@@ -1357,16 +1379,17 @@ int launch_sdegree(const kcl_graph *g, uint32_t k, Workspace &w, const uint32_t 
         unsigned *q = w.queue + c;
         const uint32_t gl = la.listing ? g->tuning.sdegree_gallop_list[c] : g->tuning.sdegree_gallop[c];
         const uint32_t bm = g->tuning.sdegree_bitmap[c];
+        const uint32_t dw = g->tuning.sdegree_cta_warps[c];
         const int ns = g->num_sms;
         class_mark(la, c, 0, s);
         if (c < kWarpClasses) {
             // listing hashes every clique: a root's cost grows with its clique
             // count, so listing shares each root's children over a CTA of 4 warps
-            if (la.listing) launch_cta<true>(k, D, w, begin, end, q, em, la.per_root, ns, gl, bm, s);
-            else launch_warp_local<false>(k, D, w, begin, end, q, em, la.per_root, ns, gl, s);
+            if (la.listing) launch_cta<true>(k, D, w, begin, end, q, em, la.per_root, ns, gl, bm, dw, s);
+            else launch_warp_local<false>(k, D, w, begin, end, q, em, la.per_root, ns, gl, bm, s);
         } else if (c < kCtaClasses) {
-            if (la.listing) launch_cta<true>(k, D, w, begin, end, q, em, la.per_root, ns, gl, bm, s);
-            else launch_cta<false>(k, D, w, begin, end, q, em, la.per_root, ns, gl, bm, s);
+            if (la.listing) launch_cta<true>(k, D, w, begin, end, q, em, la.per_root, ns, gl, bm, dw, s);
+            else launch_cta<false>(k, D, w, begin, end, q, em, la.per_root, ns, gl, bm, dw, s);
         } else {
             if (la.listing) launch_global_lists<true>(k, D, w, begin, end, q, em, la.per_root, ns, gl, s);
             else launch_global_lists<false>(k, D, w, begin, end, q, em, la.per_root, ns, gl, s);

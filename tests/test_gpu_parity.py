@@ -354,9 +354,12 @@ def test_autotune_keeps_results(kcl, small_workload):
     assert kcl.kcl_get_tuning(g) == t
     assert all(v in (0, 40, 80, 160, 400) for v in t["sdegree_gallop"] + t["sdegree_gallop_list"])
     assert all(v in (0, 4, 64, 0xFFFFFFFF) for v in t["sdegree_bitmap"])
+    assert all(v in (0, 4, 8) for v in t["sdegree_cta_warps"] + t["bitcol_cta_warps"])
     assert kcl.kcl_count(g, 5, "degree") == oracle.plain(rp, col, 5)[0]
     assert kcl.kcl_list(g, 4, "degree", None)[:2] == oracle.plain(rp, col, 4)
-    assert kcl.kcl_autotune(g, 5, "color") == t
+    tc = kcl.kcl_autotune(g, 5, "color")
+    assert {f: tc[f] for f in tc if f != "bitcol_cta_warps"} == {f: t[f] for f in t if f != "bitcol_cta_warps"}
+    assert kcl.kcl_count(g, 5, "color") == oracle.plain(rp, col, 5)[0]
 
 
 # ------------------------------------------------------ ablation switches
@@ -397,14 +400,14 @@ def test_scratch_bytes_grow_with_the_call(kcl, small_workload):
 
 @pytest.mark.parametrize("bitmap", [1, 0xFFFFFFFF])
 def test_sdegree_bitrow_and_list_forms_agree(kcl, bitmap):
-    """SDegree's CTA classes on bit-rows (threshold 1: whenever the rows fit)
-    and on lists only: identical counts and checksums."""
+    """SDegree on bit-rows (threshold 1: whenever the rows fit; warp-per-root
+    and CTA classes) and on lists only: identical counts and checksums."""
     tune = {"sdegree_bitmap": [bitmap] * kcl.KCL_MAX_CLASSES}
-    for n in (300, 700):
+    for n in (40, 100, 300, 700):
         rp, col = _near_complete(n)
         g = kcl.kcl_load_csr(rp, col)
         kcl.kcl_set_tuning(g, tune)
-        for k in (4, 5) if n <= 300 else (4,):
+        for k in (4, 5, 7) if n <= 100 else (4, 5) if n <= 300 else (4,):
             want = math.comb(n, k) - math.comb(n - 2, k - 2)
             assert kcl.kcl_count(g, k, "degree") == want
             assert kcl.kcl_list(g, k, "degree", None)[0] == want
@@ -417,3 +420,21 @@ def test_sdegree_bitrow_and_list_forms_agree(kcl, bitmap):
             ref = oracle.plain(rp, col, k)
             assert kcl.kcl_count(g, k, "degree") == ref[0]
             assert kcl.kcl_list(g, k, "degree", None)[:2] == ref
+
+
+@pytest.mark.parametrize("warps", [1, 3])
+def test_warps_per_root_keep_results(kcl, warps):
+    """One warp per root (NodeParallel) and three: identical results in both
+    orderings' CTA classes, counting and listing."""
+    tune = {"sdegree_cta_warps": [warps] * kcl.KCL_MAX_CLASSES,
+            "bitcol_cta_warps": [warps] * kcl.KCL_MAX_CLASSES}
+    for size, p in ((170, 0.6), (260, 0.45)):
+        rp, col = kclgen.chung_lu(3000, 12000, 2.3, groups=3, group_size=(size, size), group_p=p,
+                                  seed=size)
+        g = kcl.kcl_load_csr(rp, col)
+        kcl.kcl_set_tuning(g, tune)
+        for k in (3, 4, 5):
+            ref = oracle.plain(rp, col, k)
+            for o in ORDS:
+                assert kcl.kcl_count(g, k, o) == ref[0], (k, o)
+                assert kcl.kcl_list(g, k, o, None)[:2] == ref, (k, o)
