@@ -138,33 +138,25 @@ __device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
 
 // Hash of the clique R + {a, b} (a != b, neither in R): the SplitMix64
 // chain over its ids in ascending order, R's k-2 ids ascending in
-// sortedR[0..nr).  The ids are merged on the fly (no record array, so nothing
-// spills to local memory); when out is not null the ascending record is
-// written there (k ids).  seed = hash_seed(k).
+// sortedR[0..nr).  The ids are merged on the fly in exactly k = nr + 2 steps
+// with selects only, so the lanes of a warp stay converged through the k
+// mixing rounds and nothing spills to local memory; when out is not null
+// the ascending record is written there (k ids).  seed = hash_seed(k).
 __device__ __forceinline__ uint64_t clique_hash2(const uint32_t *sortedR, uint32_t nr, uint32_t a,
                                                  uint32_t b, uint64_t seed, uint32_t *out) {
-    const uint32_t lo = a < b ? a : b, hi = a < b ? b : a;
+    uint32_t e = a < b ? a : b;        // the smaller extra id first
+    const uint32_t hi = a < b ? b : a;
+    uint32_t ne = 2, ri = 0;
     uint64_t h = seed;
-    uint32_t ri = 0, o = 0;
-    uint32_t x = ri < nr ? sortedR[ri] : 0xFFFFFFFFu;
-    while (x < lo) {
+    for (uint32_t z = 0; z < nr + 2; z++) {
+        const uint32_t r = ri < nr ? sortedR[ri] : 0xFFFFFFFFu;
+        const bool take_e = ne > 0 && e < r;
+        const uint32_t x = take_e ? e : r;
+        ri += take_e ? 0u : 1u;
+        ne -= take_e ? 1u : 0u;
+        e = take_e ? hi : e;
         h = mix64(h ^ (uint64_t)x);
-        if (out) out[o++] = x;
-        x = ++ri < nr ? sortedR[ri] : 0xFFFFFFFFu;
-    }
-    h = mix64(h ^ (uint64_t)lo);
-    if (out) out[o++] = lo;
-    while (x < hi) {
-        h = mix64(h ^ (uint64_t)x);
-        if (out) out[o++] = x;
-        x = ++ri < nr ? sortedR[ri] : 0xFFFFFFFFu;
-    }
-    h = mix64(h ^ (uint64_t)hi);
-    if (out) out[o++] = hi;
-    while (ri < nr) {
-        h = mix64(h ^ (uint64_t)x);
-        if (out) out[o++] = x;
-        x = ++ri < nr ? sortedR[ri] : 0xFFFFFFFFu;
+        if (out) out[z] = x;
     }
     return h;
 }
