@@ -57,7 +57,9 @@ typedef enum {
 /* Vertex orderings of the two algorithms.
  * KCL_ORDER_DEGREE: SDegree (Algorithm 5, Section VI).  Pre-Core, Pre-List,
  *   then the DAG u -> v iff (d_u, u) < (d_v, v) with degrees of the reduced
- *   graph, and SDegreeList with sorted-list intersections N+_v and C.
+ *   graph, and SDegreeList with sorted-list intersections N+_v and C (on
+ *   the out-neighbour-reduced lists; dense subproblems may run the same
+ *   intersections on bit-rows, see kcl_tuning).
  * KCL_ORDER_COLOR: BitCol (Algorithm 6, Section VII).  Pre-Core, Pre-List,
  *   the degeneracy DAG (bulk peel rounds: eta = (round, id)), then for each
  *   root the subgraph induced by its out-neighbours, greedy colour ordering
@@ -107,7 +109,8 @@ uint32_t kcl_num_vertices(const kcl_graph *g);
 uint64_t kcl_num_edges(const kcl_graph *g);   /* undirected edges */
 
 /* Count the k-cliques of g (Algorithms 5 and 6 with Pre-Core and Pre-List,
- * Sections V-VII).  k in [3, KCL_MAX_K].  *count receives the exact count.
+ * Sections V-VII, unless switched off by kcl_set_options).  k in [3,
+ * KCL_MAX_K].  *count receives the exact count.
  * KCL_EOVERFLOW if it exceeds 2^64 - 1; KCL_ELIMIT if a root's out-degree
  * exceeds KCL_MAX_OUTDEG. */
 kcl_status kcl_count(kcl_graph *g, uint32_t k, kcl_ordering ord, uint64_t *count);
