@@ -332,12 +332,13 @@ KERNEL_NAMES = {
 # changes, until a new capture exists.
 _DRAM = "profiles/dram_listing_kernels_rmat20.md"
 TRAFFIC = {
-    (5, "degree", "count", 3): (31.54e6, _DRAM),
+    (5, "degree", "count", 3): (31.58e6, _DRAM),
+    (5, "degree", "count", 4): (34.99e6, _DRAM),
     (5, "degree", "count", 5): (14.36e6, _DRAM),
-    (4, "degree", "list", 4): (35.97e6, _DRAM),
-    (4, "degree", "list", 5): (14.48e6, _DRAM),
-    (4, "color", "list", 4): (31.27e6, _DRAM),
-    (4, "color", "list", 5): (13.65e6, _DRAM),
+    (4, "degree", "list", 4): (37.08e6, _DRAM),
+    (4, "degree", "list", 5): (14.76e6, _DRAM),
+    (4, "color", "list", 4): (31.57e6, _DRAM),
+    (4, "color", "list", 5): (13.62e6, _DRAM),
 }
 
 
