@@ -352,6 +352,7 @@ kcl_status run_call(kcl_graph *g, uint32_t k, kcl_ordering ord, const kcl_ring *
     la.per_root = per_root;
     la.per_root_cks = listing ? per_root_cks : nullptr;
     la.idmap = idmap;
+    la.max_outdeg = fe.max_outdeg;
     if (g->timing.enabled) la.class_ev = g->timing.cev;
     if (listing && ring) {
         la.ring = ring->capacity ? ring->ids : nullptr;

@@ -47,18 +47,20 @@ __host__ __device__ inline uint32_t b_stride(uint32_t W) {
     return W >= 4 ? (((W >> 2) & 1) ? W : W + 4) : a_stride(W);
 }
 
-__host__ __device__ inline SubLay sub_layout(uint32_t W, bool a_global, bool b_global) {
+// D: rows (vertices) the layout holds, at most 32 W (0 = 32 W); a class
+// whose largest out-degree is below its limit is laid out for that degree.
+__host__ __device__ inline SubLay sub_layout(uint32_t W, bool a_global, bool b_global, uint32_t D = 0) {
     SubLay L;
     L.W = W;
-    L.D = 32 * W;
+    L.D = D ? D : 32 * W;
     L.WP = a_stride(W);
     L.WPB = b_stride(W);
     L.NBR = 0;
     L.PRE = L.NBR + L.D;        // D + 1
     L.IDS = L.PRE + L.D + 1;    // D
-    L.HK = L.IDS + L.D;         // 2D hash keys
-    L.HV = L.HK + 2 * L.D;      // 2D hash values (u16)
-    L.U16 = L.HV + L.D;         // colour_old, old2new, colp (D each), start (D + 2), u16
+    L.HK = L.IDS + L.D;                 // hash keys (hash_cap(D))
+    L.HV = L.HK + hash_cap(L.D);        // hash values, u16 (hash_cap(D))
+    L.U16 = L.HV + hash_cap(L.D) / 2;   // colour_old, old2new, colp (D each), start (D + 2), u16
     L.META = L.U16 + (4 * L.D + 2 + 1) / 2;
     L.PEND = L.META + 8;        // first-level children (u16, D)
     uint32_t end = L.PEND + (L.D + 1) / 2;
@@ -648,7 +650,7 @@ __global__ void __launch_bounds__(128) k_bitcol_warp(uint32_t k, const uint32_t 
 // a global arena slice when they do not fit), then the root's first-level
 // children are handed out to the warps, heaviest first.
 template <int NW, bool LIST, bool AG, bool BG>
-__global__ void __launch_bounds__(NW * 32) k_bitcol_cta(uint32_t k, uint32_t W,
+__global__ void __launch_bounds__(NW * 32) k_bitcol_cta(uint32_t k, uint32_t W, uint32_t D,
                                                        const uint32_t *__restrict__ optr,
                                                        const uint32_t *__restrict__ oadj,
                                                        const uint32_t *__restrict__ roots,
@@ -662,7 +664,7 @@ __global__ void __launch_bounds__(NW * 32) k_bitcol_cta(uint32_t k, uint32_t W,
     // warps that walk the root's children: all of them (EdgeParallel units
     // shared out) unless the tuning caps it (1 = one warp per root)
     const uint32_t nd = em.dfs_warps && em.dfs_warps < (blockDim.x >> 5) ? em.dfs_warps : (blockDim.x >> 5);
-    const SubLay L = sub_layout(W, AG, BG);
+    const SubLay L = sub_layout(W, AG, BG, D);
     const size_t rows_a = (size_t)L.D * L.WP, rows_b = (size_t)L.D * L.WPB;
     uint32_t *slice = arena + (size_t)blockIdx.x * ((AG ? rows_a : 0) + (BG ? rows_b : 0));
     uint32_t *Ag = AG ? slice : nullptr;
@@ -741,24 +743,51 @@ constexpr ClassCfg kClass[] = {
 constexpr int kNumClasses = 8;
 
 constexpr size_t kSmemCap = 220 * 1024;
+constexpr size_t kSmemHalf = 112 * 1024;  // two CTAs per SM
 
 // Warps per CTA for class c at this k: the configured count, reduced until
 // the subproblem plus one DFS stack per warp fits in shared memory.
-int class_warps(int c, uint32_t k) {
+// Layout of CTA class c when its largest out-degree is maxd: rows for
+// round32(maxd) vertices and round4(words) words per row (at most the
+// class's own W and 32 W).
+void class_layout(int c, uint32_t maxd, uint32_t *W, uint32_t *D) {
+    const ClassCfg &cc = kClass[c];
+    uint32_t d = maxd < 32 * cc.W ? maxd : 32 * cc.W;
+    uint32_t dd = (d + 31) & ~31u;
+    if (dd < 32) dd = 32;
+    uint32_t w = (((dd >> 5) + 3) & ~3u);
+    if (w > cc.W) w = cc.W;
+    *W = w;
+    *D = dd;
+}
+
+int class_warps(int c, uint32_t k, uint32_t W, uint32_t D) {
     const ClassCfg &cc = kClass[c];
     if (!cc.cta) return cc.nw;
-    size_t sub = (size_t)sub_layout(cc.W, cc.ag, cc.bg).total * 4;
-    size_t per = (size_t)dfs_words(cc.W, k) * 4;
+    size_t sub = (size_t)sub_layout(W, cc.ag, cc.bg, D).total * 4;
+    size_t per = (size_t)dfs_words(W, k) * 4;
     int nw = cc.nw;
+    // fewer warps when that lets two CTAs share an SM and keeps at least
+    // half of them (more resident warps per SM in total)
+    const size_t half = kSmemHalf;
+    const int nw2 = half > sub ? (int)((half - sub) / per) : 0;
+    if (nw2 < nw && 2 * nw2 >= nw) nw = nw2;
     while (nw > 1 && sub + nw * per > kSmemCap) nw--;
     return nw;
 }
+int class_warps(int c, uint32_t k) { return class_warps(c, k, kClass[c].W, 32 * kClass[c].W); }
 
-size_t class_smem(int c, uint32_t k) {
+size_t class_smem(int c, uint32_t k, uint32_t W, uint32_t D) {
     const ClassCfg &cc = kClass[c];
     if (!cc.cta) return (size_t)cc.nw * (sub_layout(cc.W, false, false).total + dfs_words(cc.W, k)) * 4;
-    return ((size_t)sub_layout(cc.W, cc.ag, cc.bg).total + (size_t)class_warps(c, k) * dfs_words(cc.W, k)) * 4;
+    return ((size_t)sub_layout(W, cc.ag, cc.bg, D).total + (size_t)class_warps(c, k, W, D) * dfs_words(W, k)) * 4;
 }
+size_t class_smem(int c, uint32_t k) { return class_smem(c, k, kClass[c].W, 32 * kClass[c].W); }
+
+// Arena slices per SM of a class whose rows spill: two for the class that
+// keeps B in shared memory (two CTAs may then share an SM), one for the
+// largest classes (A and B in the arena).
+uint32_t arena_slices_per_sm(int c) { return (kClass[c].ag && !kClass[c].bg) ? 2u : 1u; }
 
 size_t class_arena_per_cta(int c) {
     const ClassCfg &cc = kClass[c];
@@ -782,7 +811,7 @@ void launch_warp(uint32_t k, Workspace &w, uint32_t begin, uint32_t end, unsigne
 }
 
 template <int NW, bool LIST, bool AG, bool BG>
-void launch_cta(uint32_t k, uint32_t W, int nw, Workspace &w, uint32_t begin, uint32_t end,
+void launch_cta(uint32_t k, uint32_t W, uint32_t D, int nw, Workspace &w, uint32_t begin, uint32_t end,
                 unsigned *q, const Emit &em, unsigned long long *per_root, size_t smem,
                 uint32_t blocks, int num_sms, cudaStream_t s) {
     auto kern = k_bitcol_cta<NW, LIST, AG, BG>;
@@ -793,7 +822,7 @@ void launch_cta(uint32_t k, uint32_t W, int nw, Workspace &w, uint32_t begin, ui
     if (occ < 1) occ = 1;
     uint32_t cap = (uint32_t)num_sms * occ;
     if (blocks > cap) blocks = cap;
-    kern<<<blocks, nw * 32, smem, s>>>(k, W, w.optr, w.oadj, w.roots, begin, end, q, w.arena, em,
+    kern<<<blocks, nw * 32, smem, s>>>(k, W, D, w.optr, w.oadj, w.roots, begin, end, q, w.arena, em,
                                        per_root, w.res);
 }
 
@@ -811,7 +840,7 @@ size_t bitcol_arena_words(uint32_t k, int num_sms, uint32_t max_outdeg) {
     size_t need = 0;
     for (int c = 0; c < kNumClasses; c++) {
         if (c > 0 && 32 * kClass[c - 1].W >= max_outdeg) break;
-        size_t words = class_arena_per_cta(c) * (size_t)num_sms;
+        size_t words = class_arena_per_cta(c) * (size_t)num_sms * arena_slices_per_sm(c);
         if (words > need) need = words;
     }
     return need;
@@ -831,7 +860,9 @@ int launch_bitcol(const kcl_graph *g, uint32_t k, Workspace &w, const uint32_t *
         const ClassCfg &cc = kClass[c];
         unsigned *q = w.queue + c;
         em.dfs_warps = g->tuning.bitcol_cta_warps[c];
-        const size_t smem = class_smem(c, k);
+        uint32_t Wl = cc.W, Dl = 32 * cc.W;
+        if (cc.cta) class_layout(c, la.max_outdeg, &Wl, &Dl);
+        const size_t smem = cc.cta ? class_smem(c, k, Wl, Dl) : class_smem(c, k);
         class_mark(la, c, 0, s);
         if (!cc.cta && la.listing) {
             // listing: every clique is hashed one by one, so a root's cost grows
@@ -840,8 +871,8 @@ int launch_bitcol(const kcl_graph *g, uint32_t k, Workspace &w, const uint32_t *
             const size_t sm4 = ((size_t)sub_layout(cc.W, false, false).total + 4 * dfs_words(cc.W, k)) * 4;
             uint32_t blocks = (uint32_t)g->num_sms * 8;
             if (blocks > end - begin) blocks = end - begin;
-            launch_cta<4, true, false, false>(k, cc.W, 4, w, begin, end, q, em, la.per_root, sm4,
-                                              blocks, g->num_sms, s);
+            launch_cta<4, true, false, false>(k, cc.W, 32 * cc.W, 4, w, begin, end, q, em, la.per_root,
+                                              sm4, blocks, g->num_sms, s);
         } else if (!cc.cta) {
 #define KCL_W(WV)                                                                              \
     if (la.listing) launch_warp<WV, true>(k, w, begin, end, q, em, la.per_root, cc.nw, smem, g->num_sms, s); \
@@ -851,12 +882,13 @@ int launch_bitcol(const kcl_graph *g, uint32_t k, Workspace &w, const uint32_t *
             else { KCL_W(4) }
 #undef KCL_W
         } else {
-            uint32_t blocks = (cc.ag || cc.bg) ? (uint32_t)g->num_sms : (uint32_t)g->num_sms * 4;
+            uint32_t blocks = (cc.ag || cc.bg) ? (uint32_t)g->num_sms * arena_slices_per_sm(c)
+                                               : (uint32_t)g->num_sms * 4;
             if (blocks > end - begin) blocks = end - begin;
-            const int nw = class_warps(c, k);
+            const int nw = class_warps(c, k, Wl, Dl);
 #define KCL_C(NWV, AGV, BGV)                                                                          \
-    if (la.listing) launch_cta<NWV, true, AGV, BGV>(k, cc.W, nw, w, begin, end, q, em, la.per_root, smem, blocks, g->num_sms, s); \
-    else launch_cta<NWV, false, AGV, BGV>(k, cc.W, nw, w, begin, end, q, em, la.per_root, smem, blocks, g->num_sms, s);
+    if (la.listing) launch_cta<NWV, true, AGV, BGV>(k, Wl, Dl, nw, w, begin, end, q, em, la.per_root, smem, blocks, g->num_sms, s); \
+    else launch_cta<NWV, false, AGV, BGV>(k, Wl, Dl, nw, w, begin, end, q, em, la.per_root, smem, blocks, g->num_sms, s);
             if (cc.nw == 8) { KCL_C(8, false, false) }
             else if (cc.nw == 16 && !cc.ag) { KCL_C(16, false, false) }
             else if (cc.nw == 16) { KCL_C(16, true, false) }

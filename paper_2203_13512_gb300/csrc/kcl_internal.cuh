@@ -223,6 +223,14 @@ __device__ __forceinline__ int hash_find(const uint32_t *hk, const uint16_t *hv,
     }
 }
 
+// Hash table slots a layout for up to D vertices must hold: the smallest
+// power of two >= 2 D (hash_size's T for every d <= D).
+__host__ __device__ inline uint32_t hash_cap(uint32_t D) {
+    uint32_t t = 2;
+    while (t < 2 * D) t <<= 1;
+    return t;
+}
+
 // Smallest power of two >= 2 * d (at least 2) and its hash shift.
 __device__ __forceinline__ void hash_size(uint32_t d, uint32_t *T, uint32_t *shift) {
     uint32_t t = 2, lg = 1;
@@ -313,6 +321,7 @@ struct ListArgs {
     unsigned long long *per_root_cks = nullptr;  // listing: checksum per root
     const uint32_t *idmap = nullptr;             // listing: vertex -> output id
     cudaEvent_t *class_ev = nullptr;             // timing: 2 events per class, or null
+    uint32_t max_outdeg = 0;                     // largest root out-degree of the call
 };
 // Records class_ev[2c] / [2c+1] (when timing) around the launch of class c.
 inline void class_mark(const ListArgs &la, int c, int end, cudaStream_t s) {

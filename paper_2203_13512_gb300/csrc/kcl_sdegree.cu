@@ -231,9 +231,9 @@ __host__ __device__ inline LLay make_llayout(uint32_t D, uint32_t k, bool list) 
     L.LOFS = D;
     L.PRE = L.LOFS + D + 1;   // prefix sums of the members' out-degrees
     L.RS = L.PRE + D + 1;     // row starts of the members' out-lists
-    L.HK = L.RS + D;          // hash keys (2D)
-    L.HV = L.HK + 2 * D;      // hash values, u16 (2D)
-    L.LEN = L.HV + D;         // list lengths, u16 (D)
+    L.HK = L.RS + D;                    // hash keys (hash_cap(D))
+    L.HV = L.HK + hash_cap(D);          // hash values, u16 (hash_cap(D))
+    L.LEN = L.HV + hash_cap(D) / 2;     // list lengths, u16 (D)
     L.RK = L.LEN + D / 2;     // DAG rank of each member, u16 (D)
     L.BITS = L.RK + D / 2;    // directed bit-rows (D x WPD)
     L.LADJ = (L.BITS + D * L.WPD + 3) & ~3u;
@@ -931,9 +931,9 @@ __host__ __device__ inline CLay make_clayout(uint32_t D) {
     L.RS = L.NBR + D;
     L.PRE = L.RS + D;          // D + 1
     L.LOFS = L.PRE + D + 1;    // D + 1
-    L.HK = L.LOFS + D + 1;     // 2D
-    L.HV = L.HK + 2 * D;       // 2D u16
-    L.LEN = L.HV + D;          // D u16: list lengths
+    L.HK = L.LOFS + D + 1;              // hash_cap(D)
+    L.HV = L.HK + hash_cap(D);          // hash_cap(D) u16
+    L.LEN = L.HV + hash_cap(D) / 2;     // D u16: list lengths
     L.RK = L.LEN + D / 2;      // D u16: DAG rank of each member
     L.P0 = L.RK + D / 2;       // D u16: first-level children
     L.META = L.P0 + D / 2;     // 16 words
@@ -1375,7 +1375,10 @@ int launch_sdegree(const kcl_graph *g, uint32_t k, Workspace &w, const uint32_t 
         uint32_t begin = class_begin[c];
         uint32_t end = c ? class_begin[c - 1] : class_begin[n_classes];
         if (end <= begin) continue;
+        // the CTA form is laid out for the class's largest out-degree
         uint32_t D = kClassD[c];
+        if (c < kCtaClasses && la.max_outdeg < D) D = (la.max_outdeg + 31) & ~31u;
+        if (D < 32) D = 32;
         unsigned *q = w.queue + c;
         const uint32_t gl = la.listing ? g->tuning.sdegree_gallop_list[c] : g->tuning.sdegree_gallop[c];
         const uint32_t bm = g->tuning.sdegree_bitmap[c];
