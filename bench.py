@@ -119,9 +119,11 @@ def run_ours(args, rank, world):
     rp, col = workload()
     n, nnz = len(rp) - 1, len(col)
     g = kcl.kcl_load_csr(rp, col)
-    # the library's autotuner picks SDegree's leaf form per out-degree class
-    # on the heaviest degree-ordered call (untimed, like the warm-up)
+    # the library's autotuner picks, per out-degree class, SDegree's
+    # bitmap-versus-list threshold and leaf form and both paths' warps per
+    # subproblem, on the heaviest calls (untimed, like the warm-up)
     kcl.kcl_autotune(g, max(k for k, o, m in STEP_PLAN if o == "degree" and m == "count"), "degree")
+    kcl.kcl_autotune(g, max(k for k, o, m in STEP_PLAN if o == "color" and m == "count"), "color")
     tuning = kcl.kcl_autotune(g, max(k for k, o, m in STEP_PLAN if o == "degree" and m == "list"),
                               "degree", listing=True)
     kcl.kcl_enable_timing(g, True)
