@@ -114,3 +114,20 @@ def test_bitmap_word_size_does_not_change_results(fig1):
     for L in (1, 3, 5, 24, 32):
         r = oracle.bitcol(rp, col, 3, L=L)
         assert (r["count"], r["checksum"]) == ref
+
+
+def test_example4_merge_work(fig1):
+    """Lemma 2's cost model on Example 4, by hand from the trace above and the
+    pinned out-degrees d+ = {v1: 0, v2: 4, v3: 2, v4: 2, v5: 3, v6: 1}: a
+    candidate v of a call at level l is merged (|C| + d+_v elements) unless
+    d+_v <= l - 2.
+      (3, [2], {1,3,4,6}): v3 4+2, v4 4+2 (v1, v6 pruned)  -> 12, 2 joins
+      (2, [2,3], {1,4}):   v4 2+2                          ->  4, 1 join
+      (2, [2,4], {1,6}):   v6 2+1                          ->  3, 1 join
+      (3, [5], {1,3,6}):   v3 3+2                          ->  5, 1 join
+    The roofline of the degree-ordered path counts exactly these elements."""
+    rp, col = fig1
+    r = oracle.sdegree(rp, col, 4, count_only=True)
+    assert r["counters"]["merge_elems"] == 12 + 4 + 3 + 5
+    assert r["counters"]["intersections"] == 5
+    assert r["counters"]["roots"] == 2 and r["counters"]["max_outdeg"] == 4

@@ -269,3 +269,21 @@ def test_count_only_mode_matches_enumeration(k):
         assert fast["count"] == full["count"] == oracle.plain(rp, col, k)[0]
         assert fast["counters"] == full["counters"]
         assert np.array_equal(fast["per_root"], full["per_root"])
+
+
+@pytest.mark.parametrize("L,k,joins,words", [(32, 3, 10, 10), (32, 4, 16, 16), (3, 4, 16, 30)])
+def test_bitjoin_work_closed_form_on_K6(L, k, joins, words):
+    """BitCol's work counters on K_6 without preprocessing, derived by hand.
+    Every vertex has degree 5, so the bulk peel removes all of them in round
+    0 and the DAG is by id: root u has h = 5 - u out-neighbours, G_u is K_h,
+    the greedy colouring gives local vertex i colour i + 1 and B(i) = {0..i-1}.
+    k = 3: the roots with h >= 2 join every v >= 1 once: sum (h - 1) over
+    h = 2..5 = 10 joins.  k = 4: roots with h >= 3; each v >= 2 is joined at
+    level 3 and its C' = {0..v-1} (size v >= 2) recurses with v - 1 joins, so
+    a root costs sum_{v=2}^{h-1} v: 9 + 5 + 2 = 16 joins.  Each join touches
+    ceil(h / L) words: 16 at L = 32; 9*2 + 5*2 + 2*1 = 30 at L = 3."""
+    rp, col = complete(6)
+    r = oracle.bitcol(rp, col, k, preprocess=False, L=L, count_only=True)
+    assert r["count"] == comb(6, k)
+    assert r["counters"]["intersections"] == joins
+    assert r["counters"]["bitjoin_words"] == words
