@@ -334,11 +334,6 @@ KERNEL_NAMES = {
 # changes, until a new capture exists.
 _DRAM = "profiles/dram_listing_kernels_rmat20.md"
 TRAFFIC = {
-    (5, "degree", "count", 3): (31.80e6, _DRAM),
-    (5, "degree", "count", 4): (35.22e6, _DRAM),
-    (5, "degree", "count", 5): (13.57e6, _DRAM),
-    (4, "degree", "list", 4): (35.83e6, _DRAM),
-    (4, "degree", "list", 5): (13.97e6, _DRAM),
     (4, "color", "list", 4): (31.20e6, _DRAM),
     (4, "color", "list", 5): (13.73e6, _DRAM),
 }

@@ -922,6 +922,11 @@ struct CLay {
     uint32_t D, WPD, NBR, RS, PRE, LOFS, HK, HV, LEN, RK, P0, META, total;
 };
 
+// Above 512 vertices the build's hash table lives in the CTA's arena slice
+// (it is dead once the rows are built), leaving shared memory to the rows,
+// lists and stacks of the DFS.
+__host__ __device__ inline bool cta_hash_global(uint32_t D) { return D > 512; }
+
 __host__ __device__ inline CLay make_clayout(uint32_t D) {
     CLay L;
     L.D = D;
@@ -931,9 +936,10 @@ __host__ __device__ inline CLay make_clayout(uint32_t D) {
     L.RS = L.NBR + D;
     L.PRE = L.RS + D;          // D + 1
     L.LOFS = L.PRE + D + 1;    // D + 1
-    L.HK = L.LOFS + D + 1;              // hash_cap(D)
+    const uint32_t hw = cta_hash_global(D) ? 0u : hash_cap(D) + hash_cap(D) / 2;
+    L.HK = L.LOFS + D + 1;              // hash_cap(D) (when in shared memory)
     L.HV = L.HK + hash_cap(D);          // hash_cap(D) u16
-    L.LEN = L.HV + hash_cap(D) / 2;     // D u16: list lengths
+    L.LEN = L.LOFS + D + 1 + hw;        // D u16: list lengths
     L.RK = L.LEN + D / 2;      // D u16: DAG rank of each member
     L.P0 = L.RK + D / 2;       // D u16: first-level children
     L.META = L.P0 + D / 2;     // 16 words
@@ -942,11 +948,18 @@ __host__ __device__ inline CLay make_clayout(uint32_t D) {
 }
 
 // arena slice per CTA: directed bit-rows (D x WPD words) + padded lists
-__host__ __device__ inline size_t cta_arena_words(uint32_t D) {
+// (+ the hash table above 512 vertices)
+__host__ __device__ inline size_t cta_arena_hash_offset(uint32_t D) {
     CLay L = make_clayout(D);
     size_t rows = ((size_t)D * L.WPD + 3) & ~(size_t)3;
     size_t lists = ((size_t)D * (D - 1) / 2 + 3 * (size_t)D + 1) / 2;
     return (rows + lists + 3) & ~(size_t)3;
+}
+
+__host__ __device__ inline size_t cta_arena_words(uint32_t D) {
+    size_t words = cta_arena_hash_offset(D);
+    if (cta_hash_global(D)) words += ((size_t)hash_cap(D) + hash_cap(D) / 2 + 3) & ~(size_t)3;
+    return words;
 }
 
 template <bool LIST>
@@ -966,13 +979,13 @@ __global__ void __launch_bounds__(512) k_sdegree_cta(uint32_t k, uint32_t D, con
     uint32_t *rs = smem + L.RS;
     uint32_t *pre = smem + L.PRE;
     uint32_t *lofs = smem + L.LOFS;
-    uint32_t *hk = smem + L.HK;
-    uint16_t *hv = reinterpret_cast<uint16_t *>(smem + L.HV);
     uint16_t *len = reinterpret_cast<uint16_t *>(smem + L.LEN);
     uint16_t *rk = reinterpret_cast<uint16_t *>(smem + L.RK);
     uint16_t *p0 = reinterpret_cast<uint16_t *>(smem + L.P0);
     uint32_t *meta = smem + L.META;
     uint32_t *slice = arena + (size_t)blockIdx.x * cta_arena_words(D);
+    uint32_t *hk = cta_hash_global(D) ? slice + cta_arena_hash_offset(D) : smem + L.HK;
+    uint16_t *hv = reinterpret_cast<uint16_t *>(cta_hash_global(D) ? hk + hash_cap(D) : smem + L.HV);
     uint32_t *bits = slice;
     uint16_t *ladj_g = reinterpret_cast<uint16_t *>(slice + (((size_t)D * L.WPD + 3) & ~(size_t)3));
     unsigned long long cnt = 0, cks = 0;
@@ -1285,10 +1298,13 @@ constexpr size_t kSmemPerBlock = 96 * 1024;
 // (listing mode's small classes) run four CTAs of 128 threads per SM.
 uint32_t cta_slices_per_sm(uint32_t D) { return D <= 128 ? 4u : 2u; }
 
-// Shared memory per CTA: up to d+ = 512 two CTAs fit on an SM (dense
-// subproblems there take the bit-row form, whose rows are at most 40 KB);
-// the largest class keeps one CTA with room for its rows or lists.
-size_t cta_smem_bytes(uint32_t D) { return D <= 128 ? 48 * 1024 : D <= 512 ? 100 * 1024 : 200 * 1024; }
+// Shared memory per CTA: up to d+ = 768 two CTAs fit on an SM (dense
+// subproblems there take the bit-row form, whose rows are at most 86 KB,
+// and above 512 the build's hash table is in the arena); beyond, one CTA
+// with room for its rows or lists.
+size_t cta_smem_bytes(uint32_t D) {
+    return D <= 128 ? 48 * 1024 : D <= 512 ? 100 * 1024 : D <= 768 ? 112 * 1024 : 200 * 1024;
+}
 int cta_threads(uint32_t D) { return D <= 128 ? 128 : 512; }
 
 template <bool LIST>
