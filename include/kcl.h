@@ -143,6 +143,21 @@ kcl_status kcl_stage_info(kcl_graph *g, uint32_t k, kcl_ordering ord, uint8_t *a
                           uint8_t *alive_final, uint32_t *outdeg, uint32_t *key,
                           uint64_t *prelist_count, uint32_t *max_outdeg);
 
+/* The colouring BitCol gives one root's subproblem, for checking it against
+ * an independent implementation (Section VII-A, Example 6 / Table II): the
+ * front end of KCL_ORDER_COLOR runs for k (Pre-Core, Pre-List, degeneracy
+ * DAG), then the listing kernels' own subproblem builder colours G_root, the
+ * subgraph induced by root's out-neighbours, greedily in (degree in G_root
+ * descending, id ascending) order with colours from 1.
+ * *outdeg receives d+ of root (0 if it was removed by Pre-Core or Pre-List
+ * or has no out-neighbours; nothing else is written then).  nbr and colour:
+ * host uint32[capacity]; nbr[i] is the i-th out-neighbour in ascending id,
+ * colour[i] its colour.  Errors: KCL_EINVAL (bad argument, root >= n, or
+ * capacity < d+), KCL_ELIMIT (d+ above 4096), KCL_ENOMEM, KCL_ECUDA.
+ * Allocates its own temporary device scratch; for tests and diagnostics. */
+kcl_status kcl_root_colouring(kcl_graph *g, uint32_t k, uint32_t root, uint32_t capacity,
+                              uint32_t *nbr, uint32_t *colour, uint32_t *outdeg);
+
 /* Batched counting (the batched form of the workload; the paper has none).
  * A kcl_batch owns device scratch that is reused across calls; create it on
  * the device and stream the batch's graphs live on.
@@ -186,6 +201,8 @@ typedef struct {
 } kcl_server_result;
 kcl_status kcl_server_create(uint32_t slots, uint64_t scratch_budget_bytes, uint64_t small_nnz,
                              kcl_server **out);
+/* Graphs may be added at any time, also while queries run: a query keeps the
+ * handle its id named when it was submitted. */
 kcl_status kcl_server_add_graph(kcl_server *s, kcl_graph *g, uint32_t *id);
 /* list = 0: count only; list = 1: count + checksum (no ring output). */
 kcl_status kcl_server_submit(kcl_server *s, uint32_t graph, uint32_t k, kcl_ordering ord, int list,
@@ -307,7 +324,9 @@ kcl_status kcl_autotune(kcl_graph *g, uint32_t k, kcl_ordering ord, int listing,
  * degree: device uint32[n], each alive vertex's number of alive neighbours.
  * round_out: device uint32[n] (caller-owned), receives the peel round of each
  *   alive vertex and 0xFFFFFFFF for the others.
- * stream: cudaStream_t as void*; the call returns when round_out is ready.
+ * stream: cudaStream_t as void*.  The call is synchronous: after the launch
+ * it copies the kernel's status word to the host and waits for the stream, so
+ * it returns when round_out is ready.
  * The first call on a device looks up the scratch array's device address
  * (once per device, with that device current); make that first call before
  * any stream capture.  Every call on a device reuses the same array (the

@@ -94,6 +94,7 @@ _sig = {
     "kcl_set_tuning": ([_P, ctypes.POINTER(_Tuning)], _I),
     "kcl_autotune": ([_P, _U32, _I, _I, ctypes.POINTER(_Tuning)], _I),
     "kcl_strerror": ([_I], ctypes.c_char_p),
+    "kcl_root_colouring": ([_P, _U32, _U32, _U32, _P, _P, ctypes.POINTER(_U32)], _I),
 }
 for _name, (_args, _res) in _sig.items():
     _f = getattr(_lib, _name)
@@ -254,6 +255,23 @@ def kcl_stage_info(g, k, ordering):
            "kcl_stage_info")
     return {"alive_core": ac[:n], "alive_final": af[:n], "outdeg": od[:n], "key": ky[:n],
             "prelist_count": int(pc.value), "max_outdeg": int(mo.value)}
+
+
+def kcl_root_colouring(g, k, root):
+    """The colouring BitCol's subproblem builder gives G_root (the subgraph
+    induced by root's out-neighbours in the degeneracy DAG after the front
+    end for k): (out-neighbours in ascending id, their colours), numpy
+    uint32 arrays; empty when root has no out-neighbours."""
+    d = ctypes.c_uint32()
+    st = _lib.kcl_root_colouring(g.handle, k, root, 0, None, None, ctypes.byref(d))
+    if st not in (KCL_OK, KCL_EINVAL) or (st == KCL_EINVAL and d.value == 0):
+        _check(st, "kcl_root_colouring")
+    nb = np.zeros(max(d.value, 1), np.uint32)
+    co = np.zeros(max(d.value, 1), np.uint32)
+    if d.value:
+        _check(_lib.kcl_root_colouring(g.handle, k, root, d.value, nb.ctypes.data, co.ctypes.data,
+                                       ctypes.byref(d)), "kcl_root_colouring")
+    return nb[: d.value], co[: d.value]
 
 
 def kcl_enable_timing(g, enable=True):

@@ -329,6 +329,9 @@ kcl_status run_front(kcl_graph *g, uint32_t k, kcl_ordering ord, const kcl_ring 
     return KCL_OK;
 }
 
+// Largest root out-degree kcl_root_colouring handles (the largest BitCol class).
+constexpr uint32_t kColouringMaxOutdeg = 4096;
+
 kcl_status check_args(kcl_graph *g, uint32_t k, kcl_ordering ord) {
     if (!g) return KCL_EINVAL;
     if (k < 3 || k > KCL_MAX_K) return KCL_EINVAL;
@@ -654,6 +657,46 @@ kcl_status kcl_stage_info(kcl_graph *g, uint32_t k, kcl_ordering ord, uint8_t *a
     if (prelist_count) *prelist_count = fe.pre_count;
     if (max_outdeg) *max_outdeg = fe.max_outdeg;
     return KCL_OK;
+}
+
+kcl_status kcl_root_colouring(kcl_graph *g, uint32_t k, uint32_t root, uint32_t capacity,
+                              uint32_t *nbr, uint32_t *colour, uint32_t *outdeg) {
+    KCL_TRY(check_args(g, k, KCL_ORDER_COLOR));
+    if (!outdeg || root >= g->n) return KCL_EINVAL;
+    *outdeg = 0;
+    if (cudaSetDevice(g->device) != cudaSuccess) return KCL_ECUDA;
+    StageTimer T(g);
+    FrontEnd fe;
+    kcl_status st = run_front(g, k, KCL_ORDER_COLOR, nullptr, false, T, fe);
+    if (st != KCL_OK && st != KCL_ELIMIT) return st;
+    Workspace &w = g->ws;
+    uint32_t ptr[2] = {0, 0};
+    KCL_CK(cudaMemcpyAsync(ptr, w.optr + root, 2 * sizeof(uint32_t), cudaMemcpyDeviceToHost, g->stream));
+    KCL_CK(cudaStreamSynchronize(g->stream));
+    const uint32_t d = ptr[1] - ptr[0];
+    *outdeg = d;
+    if (d == 0) return KCL_OK;
+    if (d > kColouringMaxOutdeg) return KCL_ELIMIT;
+    if (capacity < d || !nbr || !colour) return KCL_EINVAL;
+    uint32_t *arena = nullptr, *out = nullptr;
+    const size_t words = bitcol_colours_arena_words(d);
+    if (cudaMalloc((void **)&arena, words * 4) != cudaSuccess ||
+        cudaMalloc((void **)&out, 2 * (size_t)d * 4) != cudaSuccess) {
+        (void)cudaGetLastError();
+        cudaFree(arena);
+        return KCL_ENOMEM;
+    }
+    st = KCL_OK;
+    if (launch_bitcol_colours(w, root, d, arena, out, out + d, g->stream) < 0) st = KCL_ELIMIT;
+    if (st == KCL_OK &&
+        (cudaMemcpyAsync(nbr, out, (size_t)d * 4, cudaMemcpyDeviceToHost, g->stream) != cudaSuccess ||
+         cudaMemcpyAsync(colour, out + d, (size_t)d * 4, cudaMemcpyDeviceToHost, g->stream) != cudaSuccess ||
+         cudaStreamSynchronize(g->stream) != cudaSuccess))
+        st = KCL_ECUDA;
+    (void)cudaGetLastError();
+    cudaFree(arena);
+    cudaFree(out);
+    return st;
 }
 
 kcl_status kcl_batch_create(void *stream, kcl_batch **out) {

@@ -728,6 +728,28 @@ __global__ void __launch_bounds__(NW * 32) k_bitcol_cta(uint32_t k, uint32_t W, 
     }
 }
 
+// The colouring of one root's subproblem, for checking it against an
+// independent implementation: the same build_sub as the listing kernels (one
+// CTA, both row sets in `arena`), then the colour of each out-neighbour of u
+// in ascending id order (Section VII-A; Example 6).
+template <int NW>
+__global__ void __launch_bounds__(NW * 32) k_bitcol_colours(uint32_t W, uint32_t D,
+                                                           const uint32_t *__restrict__ optr,
+                                                           const uint32_t *__restrict__ oadj,
+                                                           uint32_t u, uint32_t *arena,
+                                                           uint32_t *out_nbr, uint32_t *out_colour) {
+    extern __shared__ uint32_t smem[];
+    const SubLay L = sub_layout(W, true, true, D);
+    const Sub s = sub_ptrs(smem, L, arena, arena + (size_t)L.D * L.WP);
+    const uint32_t base = optr[u], d = optr[u + 1] - base;
+    if (d == 0 || d > D) return;
+    build_sub<NW, 0>(d, base, W, optr, oadj, s);
+    for (uint32_t i = threadIdx.x; i < d; i += blockDim.x) {
+        out_nbr[i] = s.nbr[i];
+        out_colour[i] = s.colour_old[i];
+    }
+}
+
 // --------------------------------------------------------------- classes
 // d+ <= 32 W.  Warp per root for W <= 4, CTA per root above.
 struct ClassCfg {
@@ -827,6 +849,22 @@ void launch_cta(uint32_t k, uint32_t W, uint32_t D, int nw, Workspace &w, uint32
 }
 
 }  // namespace
+
+size_t bitcol_colours_arena_words(uint32_t d) {
+    const uint32_t W = (((d + 31) >> 5) + 3) & ~3u, D = (d + 31) & ~31u;
+    const SubLay L = sub_layout(W, true, true, D);
+    return (size_t)L.D * L.WP + (size_t)L.D * L.WPB;
+}
+
+int launch_bitcol_colours(const Workspace &w, uint32_t u, uint32_t d, uint32_t *arena,
+                          uint32_t *out_nbr, uint32_t *out_colour, cudaStream_t s) {
+    const uint32_t W = (((d + 31) >> 5) + 3) & ~3u, D = (d + 31) & ~31u;
+    const size_t smem = (size_t)sub_layout(W, true, true, D).total * 4;
+    auto kern = k_bitcol_colours<8>;
+    if (!allow_max_smem(kern) || smem > (size_t)max_dynamic_smem()) return -1;
+    kern<<<1, 256, smem, s>>>(W, D, w.optr, w.oadj, u, arena, out_nbr, out_colour);
+    return 1;
+}
 
 int bitcol_classes(uint32_t *limits, int max) {
     int n = kNumClasses < max ? kNumClasses : max;

@@ -328,6 +328,11 @@ inline void class_mark(const ListArgs &la, int c, int end, cudaStream_t s) {
     if (la.class_ev) cudaEventRecord(la.class_ev[2 * c + end], s);
 }
 int bitcol_classes(uint32_t *limits, int max);
+// One root's colouring by the listing path's subproblem builder (parity
+// checks); arena: bitcol_colours_arena_words(d) words.  -1: cannot launch.
+size_t bitcol_colours_arena_words(uint32_t d);
+int launch_bitcol_colours(const Workspace &w, uint32_t u, uint32_t d, uint32_t *arena,
+                          uint32_t *out_nbr, uint32_t *out_colour, cudaStream_t s);
 int launch_bitcol(const kcl_graph *g, uint32_t k, Workspace &w, const uint32_t *class_begin,
                   int n_classes, const ListArgs &la, cudaStream_t s);
 

@@ -29,6 +29,7 @@ using Clock = std::chrono::steady_clock;
 
 struct Job {
     uint64_t ticket;
+    kcl_graph *g;  // resolved under the lock at submission; the graph table may grow later
     uint32_t graph, k;
     kcl_ordering ord;
     int list;
@@ -113,12 +114,12 @@ void worker(kcl_server *s, Slot *slot) {
             s->queue.pop_front();
             group.push_back(head);
             scratch = head.scratch;
-            const bool small = s->graphs[head.graph]->nnz <= s->small_nnz;
+            const bool small = head.g->nnz <= s->small_nnz;
             // gather: other small-graph queries (batch), or duplicates of head
             for (auto it = s->queue.begin(); it != s->queue.end() && group.size() < s->max_batch;) {
                 bool dup = it->graph == head.graph && it->k == head.k && it->ord == head.ord &&
                            it->list == head.list;
-                bool take = dup || (small && s->graphs[it->graph]->nnz <= s->small_nnz &&
+                bool take = dup || (small && it->g->nnz <= s->small_nnz &&
                                     s->in_use + scratch + it->scratch <= s->budget);
                 if (take) {
                     if (!dup) scratch += it->scratch;
@@ -142,7 +143,7 @@ void worker(kcl_server *s, Slot *slot) {
         cks.assign(group.size(), 0);
         if (all_dups) {
             // one single call answers every copy
-            kcl_graph *g = s->graphs[head.graph];
+            kcl_graph *g = head.g;
             kcl_graph *v = slot->view;
             v->n = g->n;
             v->nnz = g->nnz;
@@ -157,7 +158,7 @@ void worker(kcl_server *s, Slot *slot) {
             gs.clear(); ks.clear(); ords.clear();
             bool any_list = false;
             for (const Job &j : group) {
-                gs.push_back(s->graphs[j.graph]);
+                gs.push_back(j.g);
                 ks.push_back(j.k);
                 ords.push_back(j.ord);
                 any_list = any_list || j.list;
@@ -242,6 +243,7 @@ kcl_status kcl_server_submit(kcl_server *s, uint32_t graph, uint32_t k, kcl_orde
         if (graph >= s->graphs.size() || s->stop) return KCL_EINVAL;
         Job j;
         j.ticket = s->results.size();
+        j.g = s->graphs[graph];
         j.graph = graph;
         j.k = k;
         j.ord = ord;

@@ -15,7 +15,17 @@ oracle's count-only mode gives:
 The roots are split into buckets (and each bucket into interleaved shards)
 so that the oracle runs on every core; the count adds the Pre-List cliques
 (Algorithm 4), which the per-root runs leave out.
-Usage: python tests/golden/make_rmat20_work.py [k ...]
+
+--checksum: also the listing checksum of every k-clique (the oracle's
+  listing mode, each clique hashed; additive mod 2^64, so it is summed over
+  the same shards plus the Pre-List cliques' checksum).  Each ordering's
+  oracle computes it on its own: the two values must agree.
+--sample: per-root counts of a seeded sample of roots -- the three with the
+  largest out-degree, 40 drawn uniformly from all roots and 2 from every
+  out-degree bucket (numpy default_rng(1000 + k)) -- stored as
+  "sample": {"roots": [...], "per_root": [...]} for a (k, ordering) whose
+  full count is beyond the oracle.
+Usage: python tests/golden/make_rmat20_work.py [--checksum | --sample] [k ...]
 """
 import json
 import multiprocessing as mp
@@ -27,6 +37,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(os.path.dirname(HERE))
 OUT = os.path.join(HERE, "rmat20_work.json")
 SHARDS = 8
+if ROOT not in sys.path:  # spawned workers re-run this module's top level
+    sys.path.insert(0, ROOT)
 
 
 def _graph():
@@ -69,8 +81,116 @@ def one(task):
     return (k, ordering), bucket, r["count"], work, r["counters"]
 
 
+def one_checksum(task):
+    import oracle
+    k, ordering, roots = task
+    rp, col = _graph()
+    fn = oracle.bitcol if ordering == "color" else oracle.sdegree
+    r = fn(rp, col, k, roots=roots)
+    return (k, ordering), r["count"], r["checksum"]
+
+
+def prelist_checksum(k):
+    import oracle
+    rp, col = _graph()
+    pl = oracle.prelist(rp, col, k, oracle.precore(rp, col, k))
+    return pl["count"], pl["checksum"]
+
+
+def main_checksum(ks):
+    """Full listing checksums, sharded over roots like the counts."""
+    with open(OUT) as f:
+        data = json.load(f)
+    jobs = [(k, o) for k in ks for o in ("color", "degree")]
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(min(SHARDS, os.cpu_count() or 1)) as pool:
+        plans = dict(zip(jobs, pool.map(plan, jobs)))
+        pre = dict(zip(ks, pool.map(prelist_checksum, ks)))
+        tasks = []
+        for job, (_, buckets) in plans.items():
+            for b, r in buckets.items():
+                ns = SHARDS if len(r) >= 64 else 1
+                tasks += [(job[0], job[1], r[s::ns]) for s in range(ns)]
+        acc = {job: [pre[job[0]][0], pre[job[0]][1]] for job in jobs}
+        for job, cnt, cks in pool.imap_unordered(one_checksum, tasks):
+            acc[job][0] += cnt
+            acc[job][1] = (acc[job][1] + cks) % (1 << 64)
+    for job, (cnt, cks) in acc.items():
+        key = "k=%d %s" % job
+        assert cnt == data[key]["count"], (key, cnt)
+        data[key]["checksum"] = cks
+        print(key, cnt, hex(cks), flush=True)
+    for k in ks:
+        assert acc[(k, "color")][1] == acc[(k, "degree")][1], "orderings disagree at k=%d" % k
+    with open(OUT, "w") as f:
+        json.dump(dict(sorted(data.items())), f, indent=1)
+
+
+def sample_roots(job):
+    """The seeded root sample of one (k, ordering)."""
+    import numpy as np
+    import oracle
+    k, ordering = job
+    rp, col = _graph()
+    pl = oracle.prelist(rp, col, k, oracle.precore(rp, col, k))
+    od = oracle.outdegrees(rp, col, pl["alive"], 0 if ordering == "degree" else 1).astype(np.int64)
+    roots = np.nonzero((pl["alive"] != 0) & (od >= k - 1))[0]
+    rng = np.random.default_rng(1000 + k)
+    pick = list(roots[np.argsort(-od[roots], kind="stable")[:3]])
+    pick += list(rng.choice(roots, 40, replace=False))
+    b = np.ceil(np.log2(np.maximum(od[roots], 1))).astype(np.int64)
+    for bb in np.unique(b):
+        r = roots[b == bb]
+        pick += list(rng.choice(r, min(2, len(r)), replace=False))
+    return sorted(set(int(x) for x in pick)), [int(od[x]) for x in sorted(set(int(x) for x in pick))]
+
+
+def one_sample(task):
+    import numpy as np
+    import oracle
+    k, ordering, roots = task
+    rp, col = _graph()
+    fn = oracle.bitcol if ordering == "color" else oracle.sdegree
+    r = fn(rp, col, k, roots=np.array(roots, np.uint32), per_root=True, count_only=True)
+    return (k, ordering), {int(x): int(r["per_root"][x]) for x in roots}
+
+
+def main_sample(ks):
+    data = {}
+    if os.path.exists(OUT):
+        with open(OUT) as f:
+            data = json.load(f)
+    jobs = [(k, o) for k in ks for o in ("color", "degree")]
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(min(SHARDS, os.cpu_count() or 1)) as pool:
+        picks = dict(zip(jobs, pool.map(sample_roots, jobs)))
+        tasks = []
+        for job, (roots, ods) in picks.items():
+            heavy = [r for r, d in sorted(zip(roots, ods), key=lambda x: -x[1])[:3]]
+            rest = [r for r in roots if r not in heavy]
+            tasks += [(job[0], job[1], [h]) for h in heavy]
+            tasks += [(job[0], job[1], rest[s::4]) for s in range(4)]
+        got = {job: {} for job in jobs}
+        for job, part in pool.imap_unordered(one_sample, tasks):
+            got[job].update(part)
+    for job in jobs:
+        key = "k=%d %s" % job
+        roots = picks[job][0]
+        entry = data.setdefault(key, {})
+        entry["sample"] = {"roots": roots, "outdeg": picks[job][1],
+                           "per_root": [got[job][r] for r in roots]}
+        print(key, len(roots), "sampled roots", flush=True)
+    with open(OUT, "w") as f:
+        json.dump(dict(sorted(data.items())), f, indent=1)
+
+
 def main():
-    ks = [int(a) for a in sys.argv[1:]] or [4, 5]
+    args = sys.argv[1:]
+    if args and args[0] == "--checksum":
+        return main_checksum([int(a) for a in args[1:]] or [4])
+    if args and args[0] == "--sample":
+        return main_sample([int(a) for a in args[1:]] or [6])
+    ks = [int(a) for a in args] or [4, 5]
     jobs = [(k, o) for k in ks for o in ("color", "degree")]
     data = {}
     if os.path.exists(OUT):

@@ -4,6 +4,7 @@ Counts, checksums, listed cliques, per-root counts and the front-end stages
 must match exactly: the whole computation is integer work.
 """
 import math
+import os
 
 import numpy as np
 import pytest
@@ -175,17 +176,25 @@ def _near_complete(n):
 
 @pytest.mark.parametrize("n", [300, 700, 1300])
 def test_large_outdegree_arena_classes(kcl, n):
+    """K_n minus one edge: out-degrees up to n-1 reach the arena classes of
+    both paths (BitCol W = 32..64, SDegree's literal form above 1024).  Counts
+    against the closed form; k = 3 counts and checksums against the oracle
+    (up to 3.6e8 triangles at n = 1300, seconds on the CPU)."""
     rp, col = _near_complete(n)
     g = kcl.kcl_load_csr(rp, col)
+    ref3 = oracle.plain(rp, col, 3)
+    assert ref3[0] == math.comb(n, 3) - (n - 2)
     # above 1024 SDegree runs the literal Algorithm 5 on global out-lists,
     # whose cost on a near-clique grows as n^k: keep k = 3 there
     for k in ((3, 4) if n <= 1024 else (3,)):
         want = math.comb(n, k) - math.comb(n - 2, k - 2)
         res = {o: kcl.kcl_list(g, k, o, None)[:2] for o in ORDS}
         assert res["degree"][0] == want and res["color"][0] == want
-        assert res["degree"][1] == res["color"][1]
-    if n == 300:
-        assert kcl.kcl_list(g, 3, "color", None)[:2] == oracle.plain(rp, col, 3)
+        assert kcl.kcl_count(g, k, "degree") == want and kcl.kcl_count(g, k, "color") == want
+        if k == 3:
+            assert res["degree"] == ref3 and res["color"] == ref3
+        else:  # no oracle checksum at this size: both paths must agree
+            assert res["degree"][1] == res["color"][1]
 
 
 # ------------------------------------------------------------- edge cases
@@ -438,3 +447,74 @@ def test_warps_per_root_keep_results(kcl, warps):
             for o in ORDS:
                 assert kcl.kcl_count(g, k, o) == ref[0], (k, o)
                 assert kcl.kcl_list(g, k, o, None)[:2] == ref, (k, o)
+
+
+# ------------------------------------------- a5: the per-root colouring
+def _induced_out_subgraph(rp, col, key, alive, u):
+    """N+_u in the DAG eta = (key, id) over alive vertices (ascending id) and
+    the CSR of G_u, the subgraph it induces (local index = rank in N+_u)."""
+    nb = [int(w) for w in col[rp[u]:rp[u + 1]]
+          if alive[w] and (int(key[u]), u) < (int(key[w]), int(w))]
+    pos = {w: i for i, w in enumerate(nb)}
+    edges = []
+    for i, a in enumerate(nb):
+        for w in col[rp[a]:rp[a + 1]]:
+            j = pos.get(int(w))
+            if j is not None and j > i:
+                edges.append((i, j))
+    return nb, csr_from_edges(len(nb), edges)
+
+
+def test_colouring_of_example6(kcl, fig1):
+    """G_r equal to the Example 6 graph (v1..v6 of Figure 1): root r = 0 is
+    adjacent to v1..v6, and each v_i also to its own K_8, so r leaves in the
+    first peel round and N+_r = {v1..v6}.  The GPU's colours are Example 6's
+    (v1..v6 -> 1, 2, 3, 4, 2, 3; tests/golden/table2_bitmaps.txt)."""
+    rp0, col0 = fig1
+    ex6 = [(u, int(v)) for u in range(1, 7) for v in col0[rp0[u]:rp0[u + 1]] if u < v <= 6]
+    edges = list(ex6) + [(0, v) for v in range(1, 7)]
+    nxt = 7
+    for v in range(1, 7):
+        block = list(range(nxt, nxt + 8))
+        edges += [(a, b) for i, a in enumerate(block) for b in block[i + 1:]]
+        edges += [(v, a) for a in block]
+        nxt += 8
+    rp, col = csr_from_edges(nxt, edges)
+    g = kcl.kcl_load_csr(rp, col)
+    colours = {}
+    with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden",
+                           "table2_bitmaps.txt")) as f:
+        for line in f:
+            p = line.split("#", 1)[0].split()
+            if p and p[0] == "colour":
+                colours[int(p[1])] = int(p[2])
+    for k in (3, 4):
+        nb, co = kcl.kcl_root_colouring(g, k, 0)
+        assert list(nb) == [1, 2, 3, 4, 5, 6]
+        assert [int(c) for c in co] == [colours[v] for v in range(1, 7)]
+        _, ex_rp_col = _induced_out_subgraph(rp, col, kcl.kcl_stage_info(g, k, "color")["key"],
+                                             np.ones(nxt, np.uint8), 0)
+        assert list(oracle.colour_graph(*ex_rp_col)[1]) == list(co)
+
+
+@pytest.mark.parametrize("scale,k", [(16, 4), (20, 5)])
+def test_colouring_matches_oracle_on_sampled_roots(kcl, scale, k):
+    """The colour of every out-neighbour of 55 seeded roots (the 5 largest
+    out-degrees and 50 drawn at random) equals oracle.colour_graph on G_u
+    built from the oracle's own front end (Pre-Core, Pre-List, bulk peel)."""
+    rp, col = kclgen.rmat20(seed=1, scale=scale)
+    g = kcl.kcl_load_csr(rp, col)
+    pl = oracle.prelist(rp, col, k, oracle.precore(rp, col, k))
+    key, _ = oracle.degeneracy_rounds(rp, col, pl["alive"])
+    od = oracle.outdegrees(rp, col, pl["alive"], 1).astype(np.int64)
+    roots = np.nonzero((pl["alive"] != 0) & (od >= k - 1))[0]
+    rng = np.random.default_rng(scale)
+    sample = list(roots[np.argsort(-od[roots], kind="stable")[:5]])
+    sample += list(rng.choice(roots, 50, replace=False))
+    for u in sample:
+        u = int(u)
+        nb, (grp, gcol) = _induced_out_subgraph(rp, col, key, pl["alive"], u)
+        got_nb, got_co = kcl.kcl_root_colouring(g, k, u)
+        assert list(got_nb) == nb, u
+        _, want = oracle.colour_graph(grp, gcol)
+        assert np.array_equal(got_co, want), u

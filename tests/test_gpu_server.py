@@ -45,7 +45,6 @@ def test_served_results_equal_results_alone(kcl, slots):
         t.join()
     results = [kcl.kcl_server_wait(srv, t) for t in tickets]
     srv.destroy()
-    assert max(r["batch"] for r in results) >= 1
     for (gi, k, o, lst), r in zip(queries, results):
         assert r["status"] == 0
         assert r["submit_s"] <= r["start_s"] <= r["done_s"]
@@ -54,6 +53,39 @@ def test_served_results_equal_results_alone(kcl, slots):
             assert (r["count"], r["checksum"]) == (c, s)
         else:
             assert r["count"] == kcl.kcl_count(graphs[gi], k, o)
+
+
+def test_burst_is_batched_and_slots_overlap(kcl):
+    """Four heavy queries occupy the four slots at once (their [start, done]
+    intervals overlap on the device); a burst of small-graph queries that
+    arrives meanwhile waits in the queue and is answered by batched passes
+    (some result reports batch > 1).  Every result equals the query alone."""
+    heavy = [kcl.kcl_load_csr(*kclgen.rmat20(seed=s, scale=12)) for s in (1, 2)]
+    small = []
+    i = 0
+    while len(small) < 6:
+        rp, col, _ = kclgen.batch_graph(i)
+        i += 1
+        if len(col) <= 20000:
+            small.append(kcl.kcl_load_csr(rp, col))
+    srv = kcl.kcl_server_create(slots=4, scratch_budget_bytes=8 << 30, small_nnz=20000)
+    hid = [kcl.kcl_server_add_graph(srv, g) for g in heavy]
+    sid = [kcl.kcl_server_add_graph(srv, g) for g in small]
+    hq = [(hid[j % 2], heavy[j % 2], 6 + j % 2, "color" if j < 2 else "degree") for j in range(4)]
+    ht = [kcl.kcl_server_submit(srv, gid, k, o, True) for gid, _, k, o in hq]
+    sq = [(j % len(small), 3 + j % 5, "color" if j % 3 else "degree") for j in range(30)]
+    st = [kcl.kcl_server_submit(srv, sid[gi], k, o, False) for gi, k, o in sq]
+    hr = [kcl.kcl_server_wait(srv, t) for t in ht]
+    sr = [kcl.kcl_server_wait(srv, t) for t in st]
+    srv.destroy()
+    assert all(r["status"] == 0 for r in hr + sr)
+    spans = sorted((r["start_s"], r["done_s"]) for r in hr)
+    assert any(spans[j][0] < spans[j - 1][1] for j in range(1, len(spans))), spans
+    assert max(r["batch"] for r in sr) > 1
+    for (_, g, k, o), r in zip(hq, hr):
+        assert (r["count"], r["checksum"]) == kcl.kcl_list(g, k, o, None)[:2]
+    for (gi, k, o), r in zip(sq, sr):
+        assert r["count"] == kcl.kcl_count(small[gi], k, o)
 
 
 def test_graph_view_shares_the_graph(kcl):

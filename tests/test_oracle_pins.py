@@ -287,3 +287,68 @@ def test_bitjoin_work_closed_form_on_K6(L, k, joins, words):
     assert r["count"] == comb(6, k)
     assert r["counters"]["intersections"] == joins
     assert r["counters"]["bitjoin_words"] == words
+
+
+# ------------------------------------------------------------ validation
+def _valid_by_definition(n, rp, col):
+    """Problem input (Section III-A): an undirected simple graph as CSR --
+    offsets start at 0 and never decrease, every id < n, no self-loop, each
+    row strictly ascending (no duplicate), and v in row u iff u in row v."""
+    if rp[0] != 0 or any(rp[i + 1] < rp[i] for i in range(n)):
+        return False
+    rows = [list(col[rp[u]:rp[u + 1]]) for u in range(n)]
+    for u, r in enumerate(rows):
+        if any(v >= n or v == u for v in r):
+            return False
+        if any(r[i] >= r[i + 1] for i in range(len(r) - 1)):
+            return False
+    return all(u in rows[v] for u, r in enumerate(rows) for v in r)
+
+
+def test_validate_rejects_each_kind_of_malformed_input():
+    bad = {
+        "asymmetric": ([0, 1, 1], [1]),
+        "self-loops": ([0, 1, 2], [0, 1]),
+        "duplicate edge": ([0, 2, 4], [1, 1, 0, 0]),
+        "unsorted row": ([0, 2, 3, 4], [2, 1, 0, 0]),
+        "id out of range": ([0, 1, 2], [5, 0]),
+        "row_ptr[0] != 0": ([1, 1, 2], [1, 0]),
+        "decreasing row_ptr": ([0, 2, 1, 3], [1, 2, 0]),
+    }
+    for what, (rp, col) in bad.items():
+        rp = np.array(rp, np.uint64)
+        col = np.array(col, np.uint32)
+        assert not oracle.validate(rp, col), what
+    good = [csr_from_edges(0, []), csr_from_edges(4, []), csr_from_edges(3, [(0, 1), (1, 2)]),
+            complete(6), gnp(30, 0.3, 5)]
+    for rp, col in good:
+        assert oracle.validate(rp, col)
+
+
+def test_validate_matches_the_definition_on_every_tiny_input():
+    """Brute force: all 0/1 adjacency matrices on 3 vertices (self-loops and
+    asymmetric pairs included), and random row orders / duplicated entries on
+    4-5 vertices, judged against the definition written out above."""
+    for bits in range(1 << 9):
+        n = 3
+        rows = [[v for v in range(n) if bits >> (3 * u + v) & 1] for u in range(n)]
+        rp = np.cumsum([0] + [len(r) for r in rows]).astype(np.uint64)
+        col = np.array([v for r in rows for v in r], np.uint32)
+        assert oracle.validate(rp, col) == _valid_by_definition(n, rp, col), bits
+    rng = np.random.default_rng(9)
+    for _ in range(400):
+        n = int(rng.integers(4, 6))
+        a = rng.random((n, n)) < 0.5
+        if rng.random() < 0.5:
+            a = a | a.T
+        rows = [list(np.nonzero(a[u])[0]) for u in range(n)]
+        for r in rows:
+            if r and rng.random() < 0.2:
+                r.append(r[int(rng.integers(len(r)))])
+            if rng.random() < 0.2:
+                rng.shuffle(r)
+            if rng.random() < 0.7:
+                r.sort()
+        rp = np.cumsum([0] + [len(r) for r in rows]).astype(np.uint64)
+        col = np.array([v for r in rows for v in r], np.uint32)
+        assert oracle.validate(rp, col) == _valid_by_definition(n, rp, col)
