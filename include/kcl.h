@@ -338,6 +338,32 @@ kcl_status kcl_degeneracy_order_noalloc(uint32_t n, const uint64_t *row_ptr, con
                                         const uint8_t *alive, const uint32_t *degree,
                                         uint32_t *round_out, void *stream);
 
+/* Measured per-SM rates of the instructions the listing kernels are bound by
+ * (a measurement facility; the paper has none).  Each probe runs one CTA of
+ * 1024 threads per SM with 8 independent dependency chains per thread and
+ * times its loop with the SM's cycle counter, so every rate is per SM per SM
+ * clock; sm_clock_mhz is the probe's cycles over its CUDA-event time.
+ *   popc / lop3 / iadd: 32-bit population count, three-input logic op, add;
+ *   bitjoin_words: the BitJoin word of Algorithm 6 as the kernels run it --
+ *     a conflict-free 128-bit shared-memory read of a bit-row, a broadcast
+ *     128-bit read of the candidate set, AND, POPC and accumulate per word;
+ *   lds128_bytes: bytes of conflict-free 128-bit shared-memory loads;
+ *   mix64: SplitMix64 rounds h = f(h ^ x) of the listing checksum.
+ * Runs for a fraction of a second on `stream` (cudaStream_t as void*) and
+ * allocates a few KB of device memory.  Errors: KCL_EINVAL, KCL_ENOMEM,
+ * KCL_ECUDA. */
+typedef struct {
+    uint32_t num_sms;
+    double sm_clock_mhz;
+    double popc_per_sm_clk;
+    double lop3_per_sm_clk;
+    double iadd_per_sm_clk;
+    double bitjoin_words_per_sm_clk;
+    double lds128_bytes_per_sm_clk;
+    double mix64_per_sm_clk;
+} kcl_int_peaks;
+kcl_status kcl_measure_int_peaks(void *stream, kcl_int_peaks *out);
+
 /* Human-readable text for a status. */
 const char *kcl_strerror(kcl_status s);
 

@@ -334,6 +334,27 @@ def kcl_last_timing(g):
             {STAGES[i]: int(t.launches[i]) for i in range(KCL_NUM_STAGES)}, t.classes())
 
 
+class _IntPeaks(ctypes.Structure):
+    _fields_ = [("num_sms", ctypes.c_uint32), ("sm_clock_mhz", ctypes.c_double),
+                ("popc_per_sm_clk", ctypes.c_double), ("lop3_per_sm_clk", ctypes.c_double),
+                ("iadd_per_sm_clk", ctypes.c_double), ("bitjoin_words_per_sm_clk", ctypes.c_double),
+                ("lds128_bytes_per_sm_clk", ctypes.c_double), ("mix64_per_sm_clk", ctypes.c_double)]
+
+
+_lib.kcl_measure_int_peaks.argtypes = [_P, ctypes.POINTER(_IntPeaks)]
+_lib.kcl_measure_int_peaks.restype = _I
+
+
+def kcl_measure_int_peaks(stream=None):
+    """Measured per-SM-clock rates of POPC, LOP3, IADD, the BitJoin word,
+    128-bit shared loads and the SplitMix64 round (see include/kcl.h)."""
+    p = _IntPeaks()
+    _check(_lib.kcl_measure_int_peaks(stream if stream is not None else _current_stream(),
+                                      ctypes.byref(p)), "kcl_measure_int_peaks")
+    return {f: (int(getattr(p, f)) if f == "num_sms" else float(getattr(p, f)))
+            for f, _ in _IntPeaks._fields_}
+
+
 def kcl_strerror(status):
     return _lib.kcl_strerror(status).decode()
 

@@ -17,7 +17,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(ROOT, "_build", "kcl")
 LIB = os.path.join(HERE, "libkcl.so")
-SOURCES = ["kcl_api.cu", "kcl_prep.cu", "kcl_bitcol.cu", "kcl_sdegree.cu", "kcl_server.cu"]
+SOURCES = ["kcl_api.cu", "kcl_prep.cu", "kcl_bitcol.cu", "kcl_sdegree.cu", "kcl_server.cu",
+           "kcl_peaks.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

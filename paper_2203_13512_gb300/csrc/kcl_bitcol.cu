@@ -470,24 +470,133 @@ __device__ void leaf(const View &v, const uint32_t *C, uint32_t cw, uint32_t dep
     }
 }
 
+// |B'(q) & C| for the 32 rows q = 32 j + lane of candidate word j: the rows
+// lie below 32 (j + 1), so every lane reads the same number of words (a
+// uniform loop; rows and C are zero beyond their extents).
+__device__ __forceinline__ uint32_t word_block_popc(const View &v, const uint32_t *C, uint32_t cw,
+                                                    uint32_t j) {
+    const uint32_t q = j * 32 + lane_id();
+    const uint32_t *row = v.B + q * v.WP;
+    uint32_t x = 0;
+    if (v.W >= 4) {
+        const uint32_t nc = min((j >> 2) + 1, (cw + 3) >> 2);
+        const uint4 *r4 = reinterpret_cast<const uint4 *>(row);
+        const uint4 *c4 = reinterpret_cast<const uint4 *>(C);
+        for (uint32_t t = 0; t < nc; t++) {
+            const uint4 a = r4[t], b = c4[t];
+            x += __popc(a.x & b.x) + __popc(a.y & b.y) + __popc(a.z & b.z) + __popc(a.w & b.w);
+        }
+    } else {
+        const uint32_t nw = min(j + 1, cw);
+        for (uint32_t t = 0; t < nw; t++) x += __popc(row[t] & C[t]);
+    }
+    return x;
+}
+
 // Inner node at level l >= 3: pending children = candidates p with
 // |B'(p) & C| >= l-1, as a bitmap P[0..W).
 __device__ void expand(const View &v, const uint32_t *C, uint32_t cw, uint32_t l, uint32_t *P) {
     const unsigned lane = lane_id();
     const uint32_t s = start_of(v, l);
     for (uint32_t j = 0; j < v.W; j++) {
-        uint32_t m = j < cw ? cand_word(C, j, s) : 0u;
+        const uint32_t m = j < cw ? cand_word(C, j, s) : 0u;
         bool ok = false;
-        if ((m >> lane) & 1u) {
-            uint32_t p = j * 32 + lane;
-            const uint32_t *row = v.B + p * v.WP;
-            const uint32_t x = and_popc(row, C, row_words(v, p, cw), v.W);
-            ok = x + 1 >= l;
+        if (m) {  // all lanes read their rows (uniform); non-candidates are masked
+            const uint32_t x = word_block_popc(v, C, cw, j);
+            ok = ((m >> lane) & 1u) && x + 1 >= l;
         }
-        unsigned bal = __ballot_sync(kFull, ok);
+        const unsigned bal = __ballot_sync(kFull, ok);
         if (lane == 0) P[j] = bal;
     }
     __syncwarp();
+}
+
+// A batch of nb <= 32 (child, candidate) pairs of a level-3 node (counting):
+// lane i takes pair pq[i] = (p << 16) | q and closes |B'(q) & B'(p) & C|
+// cliques (one three-input AND per word; the rows lie below q, so the batch
+// reads a uniform number of words up to its largest q).
+__device__ __forceinline__ void pair_batch(const View &v, const uint32_t *C, uint32_t cw,
+                                           const uint32_t *pq, uint32_t nb,
+                                           unsigned long long &cnt) {
+    const unsigned lane = lane_id();
+    const uint32_t e = pq[lane < nb ? lane : nb - 1];
+    const uint32_t p = e >> 16, q = e & 0xFFFFu;
+    const uint32_t qmax = __reduce_max_sync(kFull, q);
+    const uint32_t *rq = v.B + q * v.WP, *rp = v.B + p * v.WP;
+    uint32_t x = 0;
+    if (v.W >= 4) {
+        const uint32_t nc = min((qmax >> 7) + 1, (cw + 3) >> 2);
+        const uint4 *a4 = reinterpret_cast<const uint4 *>(rq);
+        const uint4 *b4 = reinterpret_cast<const uint4 *>(rp);
+        const uint4 *c4 = reinterpret_cast<const uint4 *>(C);
+        for (uint32_t t = 0; t < nc; t++) {
+            const uint4 a = a4[t], b = b4[t], c = c4[t];
+            x += __popc(a.x & b.x & c.x) + __popc(a.y & b.y & c.y) + __popc(a.z & b.z & c.z) +
+                 __popc(a.w & b.w & c.w);
+        }
+    } else {
+        const uint32_t nw = min((qmax >> 5) + 1, cw);
+        for (uint32_t t = 0; t < nw; t++) x += __popc(rq[t] & rp[t] & C[t]);
+    }
+    if (lane < nb) cnt += x;
+}
+
+// Counting below a level-3 node with candidate set C and pending children P
+// (Algorithm 6 at levels 3 and 2): for every child p and every q in
+// B'(p) & C of colour >= 2, |B'(q) & B'(p) & C| cliques close.  All (p, q)
+// pairs of the node go through one per-warp queue of 64 entries (pq), 32 to
+// a batch, so no child materialises its C' and batches stay full across
+// children.  Cm (W words of scratch) receives C restricted to colour >= 2,
+// the leaf candidates, so the pair scan reads four masked words at a time.
+__device__ void leaf_pairs(const View &v, const uint32_t *C, uint32_t cw, const uint32_t *P,
+                           uint32_t *Cm, uint32_t *pq, unsigned long long &cnt) {
+    const unsigned lane = lane_id();
+    const uint32_t s2 = start_of(v, 2);
+    for (uint32_t t = lane; t < v.W; t += 32) Cm[t] = t < cw ? cand_word(C, t, s2) : 0u;
+    __syncwarp();
+    const unsigned lt = (1u << lane) - 1u, me = 1u << lane;
+    uint32_t pend = 0;
+    for (uint32_t jp = s2 >> 5; jp < cw; jp++) {
+        uint32_t pw = P[jp];
+        while (pw) {
+            const uint32_t p = jp * 32 + (__ffs(pw) - 1);
+            pw &= pw - 1;
+            const uint32_t ncw = min(cw, (p >> 5) + 1);  // B'(p) lies below p
+            const uint32_t *rowp = v.B + p * v.WP;
+            for (uint32_t t0 = 0; t0 < ncw; t0 += 4) {
+                uint32_t mw[4];
+                if (v.W >= 4) {
+                    const uint4 a = *reinterpret_cast<const uint4 *>(rowp + t0);
+                    const uint4 c = *reinterpret_cast<const uint4 *>(Cm + t0);
+                    mw[0] = a.x & c.x; mw[1] = a.y & c.y; mw[2] = a.z & c.z; mw[3] = a.w & c.w;
+                } else {
+#pragma unroll
+                    for (int z = 0; z < 4; z++) mw[z] = t0 + z < ncw ? rowp[t0 + z] & Cm[t0 + z] : 0u;
+                }
+#pragma unroll
+                for (int z = 0; z < 4; z++) {
+                    const uint32_t m = mw[z];
+                    if (!m) continue;
+                    const uint32_t base = (p << 16) | ((t0 + z) * 32);
+                    if (m & me) pq[pend + __popc(m & lt)] = base + lane;
+                    pend += __popc(m);
+                    if (pend >= 32) {
+                        __syncwarp();
+                        pair_batch(v, C, cw, pq, 32, cnt);
+                        __syncwarp();
+                        if (lane < pend - 32) pq[lane] = pq[32 + lane];
+                        pend -= 32;
+                        __syncwarp();
+                    }
+                }
+            }
+        }
+    }
+    if (pend) {
+        __syncwarp();
+        pair_batch(v, C, cw, pq, pend, cnt);
+        __syncwarp();
+    }
 }
 
 // The subtree below first-level child p0 of the root (C1 = B'(p0)), run by
@@ -515,6 +624,11 @@ __device__ void dfs_child(const View &v, uint32_t p0, uint32_t *stack, const Emi
         return;
     }
     expand(v, Cst + W, cw1, l, Pst + W);
+    if (!LIST && l == 3) {  // sortedR and the leaf queue (64 words) hold the pair queue
+        leaf_pairs(v, Cst + W, cw1, Pst + W, Cst + 2 * W, sortedR, cnt);
+        __syncwarp();
+        return;
+    }
     if (lane == 0) cur[1] = 0;
     uint32_t cwst[KCL_MAX_K];
     cwst[1] = cw1;
@@ -538,6 +652,10 @@ __device__ void dfs_child(const View &v, uint32_t p0, uint32_t *stack, const Emi
         uint32_t lc = k - 2 - (uint32_t)depth;  // level of the child
         if (lc == 2) {
             leaf<LIST>(v, Cn, ncw, depth + 1, 0, 1, path, sortedR, em, res, cnt, cks);
+            __syncwarp();
+        } else if (!LIST && lc == 3) {
+            expand(v, Cn, ncw, 3, Pst + (depth + 1) * W);
+            leaf_pairs(v, Cn, ncw, Pst + (depth + 1) * W, Cn + W, sortedR, cnt);
             __syncwarp();
         } else {
             expand(v, Cn, ncw, lc, Pst + (depth + 1) * W);
@@ -583,7 +701,7 @@ __device__ uint32_t root_children(const View &v, const Sub &s) {
 // --------------------------------------------------------------- kernels
 // Warp per root: subproblem and stack in this warp's slice of shared memory.
 template <int WT, bool LIST>
-__global__ void __launch_bounds__(128) k_bitcol_warp(uint32_t k, const uint32_t *__restrict__ optr,
+__global__ void __launch_bounds__(128, 8) k_bitcol_warp(uint32_t k, const uint32_t *__restrict__ optr,
                                                     const uint32_t *__restrict__ oadj,
                                                     const uint32_t *__restrict__ roots,
                                                     uint32_t begin, uint32_t end, unsigned *queue,

@@ -710,6 +710,72 @@ __device__ void bexpand(const BView &v, const uint32_t *C, uint32_t l, uint32_t 
     __syncwarp();
 }
 
+// A batch of nb <= 32 (child, candidate) pairs of a level-3 node (counting
+// on bit-rows): lane i takes pq[i] = (p << 16) | q and closes
+// |row(q) & row(p) & C| cliques.  Rows lie above their vertex, so the batch
+// reads a uniform range of words from its smallest q on.
+__device__ __forceinline__ void bpair_batch(const BView &v, const uint32_t *C, const uint32_t *pq,
+                                            uint32_t nb, unsigned long long &cnt) {
+    const unsigned lane = lane_id();
+    const uint32_t e = pq[lane < nb ? lane : nb - 1];
+    const uint32_t p = e >> 16, q = e & 0xFFFFu;
+    const uint32_t qmin = __reduce_min_sync(kFull, q);
+    uint32_t x = 0;
+    if (((v.W | v.WP) & 3u) == 0) {
+        const uint4 *a4 = reinterpret_cast<const uint4 *>(v.R + q * v.WP);
+        const uint4 *b4 = reinterpret_cast<const uint4 *>(v.R + p * v.WP);
+        const uint4 *c4 = reinterpret_cast<const uint4 *>(C);
+        for (uint32_t t = qmin >> 7; t < (v.W >> 2); t++) {
+            const uint4 a = a4[t], b = b4[t], c = c4[t];
+            x += __popc(a.x & b.x & c.x) + __popc(a.y & b.y & c.y) + __popc(a.z & b.z & c.z) +
+                 __popc(a.w & b.w & c.w);
+        }
+    } else {
+        const uint32_t *rq = v.R + q * v.WP, *rp = v.R + p * v.WP;
+        for (uint32_t t = qmin >> 5; t < v.W; t++) x += __popc(rq[t] & rp[t] & C[t]);
+    }
+    if (lane < nb) cnt += x;
+}
+
+// Counting below a level-3 node on bit-rows (Algorithm 5 at levels 3 and 2):
+// for every pending child p and every q in row(p) & C, |row(q) & row(p) & C|
+// cliques close.  All (p, q) pairs go through the per-warp queue pq (64
+// entries), 32 to a batch, so no child materialises its C'.
+__device__ void bleaf_pairs(const BView &v, const uint32_t *C, const uint32_t *P, uint32_t *pq,
+                            unsigned long long &cnt) {
+    const unsigned lane = lane_id();
+    const unsigned lt = (1u << lane) - 1u, me = 1u << lane;
+    uint32_t pend = 0;
+    for (uint32_t jp = 0; jp < v.W; jp++) {
+        uint32_t pw = P[jp];
+        while (pw) {
+            const uint32_t p = jp * 32 + (__ffs(pw) - 1);
+            pw &= pw - 1;
+            const uint32_t *rowp = v.R + p * v.WP;
+            for (uint32_t t = p >> 5; t < v.W; t++) {  // row(p) lies above p
+                const uint32_t m = rowp[t] & C[t];
+                if (!m) continue;
+                const uint32_t base = (p << 16) | (t * 32);
+                if (m & me) pq[pend + __popc(m & lt)] = base + lane;
+                pend += __popc(m);
+                if (pend >= 32) {
+                    __syncwarp();
+                    bpair_batch(v, C, pq, 32, cnt);
+                    __syncwarp();
+                    if (lane < pend - 32) pq[lane] = pq[32 + lane];
+                    pend -= 32;
+                    __syncwarp();
+                }
+            }
+        }
+    }
+    if (pend) {
+        __syncwarp();
+        bpair_batch(v, C, pq, pend, cnt);
+        __syncwarp();
+    }
+}
+
 // The subtree below first-level child p0 (C1 = row(p0)), one warp.
 template <bool LIST>
 __device__ void bdfs_child(const BView &v, uint32_t p0, uint32_t *stack, const Emit &em,
@@ -729,6 +795,11 @@ __device__ void bdfs_child(const BView &v, uint32_t p0, uint32_t *stack, const E
         return;
     }
     bexpand(v, Cst + W, k - 2, Pst + W);
+    if (!LIST && k - 2 == 3) {  // sortedR and the leaf queue (64 words) hold the pair queue
+        bleaf_pairs(v, Cst + W, Pst + W, sortedR, cnt);
+        __syncwarp();
+        return;
+    }
     if (lane == 0) cur[1] = 0;
     __syncwarp();
     int depth = 1;
@@ -748,6 +819,10 @@ __device__ void bdfs_child(const BView &v, uint32_t p0, uint32_t *stack, const E
         const uint32_t lc = k - 2 - (uint32_t)depth;  // level of the child
         if (lc == 2) {
             bleaf<LIST>(v, Cn, depth + 1, path, sortedR, em, res, cnt, cks);
+            __syncwarp();
+        } else if (!LIST && lc == 3) {
+            bexpand(v, Cn, 3, Pst + (depth + 1) * W);
+            bleaf_pairs(v, Cn, Pst + (depth + 1) * W, sortedR, cnt);
             __syncwarp();
         } else {
             bexpand(v, Cn, lc, Pst + (depth + 1) * W);
