@@ -1,19 +1,32 @@
 """Benchmark: k-cliques/s of the GB300 k-clique library on the R-MAT scale-20
 workload (2^20 vertices, 16*2^20 unique undirected edges, a=0.57 b=0.19
 c=0.19 d=0.05, seed 1), SDegree (degree ordering) and BitCol (colour
-ordering), counting mode and listing mode (count + checksum).
+ordering), counting mode and listing mode.
 
 One step = every (k, ordering, mode) call of STEP_PLAN on the resident
 graph: Pre-Core, Pre-List, orientation and the listing kernels run inside
-each call.  `value` = sum of the k-clique counts of the step / device time of
-the step (CUDA events on the stream the library runs on).  `e2e` = the same
-metric through the C ABI from pinned host buffers: graph copy-in (validated
-on the device), the step's calls and the read-back of every count/checksum.
+each call; the listing calls write every clique (k uint32 ids) into a 4 GiB
+device ring that wraps, and return the exact count and checksum.  `value` =
+sum of the k-clique counts of the step / device time of the step (CUDA
+events on the stream the library runs on).  `e2e` = the same metric through
+the C ABI from pinned host buffers: graph copy-in (validated on the device),
+the step's calls and the read-back of every count/checksum.  Every count and
+checksum is checked against the oracle's stored full-size values
+(tests/golden/rmat20_work.json); a mismatch aborts the run.
+
+After the timed steps, the k = 6 counts (both orderings) are timed once each
+(`c2_k6`: 2.8e13 cliques, seconds per call, so not part of the step); k = 7
+is out of reach of a bench run (12 s per call already at scale 17).
+
+The roofline denominators are measured by kcl_measure_int_peaks (per-SM
+rates of the BitJoin word, the SplitMix64 round, ...) times the SM count
+and the SM clock sampled during the timed region; the front-end passes are
+reported against the measured HBM copy bandwidth (MEASURED_PEAKS.json).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
---impl reference times the CPU oracle (oracle/, single thread) on a bounded
-sample of the same workload: a fixed set of roots of the same DAG.
+--impl reference times the CPU oracle (oracle/, all host cores) on a
+bounded sample of the same plan: a fixed set of roots of each call's DAG.
 Multi-GPU: the path does not shard (one graph per GPU); N ranks run
 independent replicas and `value` is the total over ranks / the slowest rank.
 """
@@ -36,8 +49,10 @@ STEP_PLAN = [  # (k, ordering, mode)
     (4, "color", "count"), (5, "color", "count"), (4, "degree", "count"), (5, "degree", "count"),
     (4, "color", "list"), (4, "degree", "list"),
 ]
+K6_PLAN = [(6, "color", "count"), (6, "degree", "count")]
 METRIC = "k-cliques/s (bit-exact counts; R-MAT scale 20, SDegree + BitCol)"
 L2_BYTES = 129 * 2 ** 20
+RING_BYTES = 4 << 30  # listing ring (wraps)
 
 
 def _peaks():
@@ -107,6 +122,24 @@ def workload():
 
 
 # --------------------------------------------------------------- our arm
+def check_golden(per_call, golden):
+    """Every count (and listing checksum) of the plan against the oracle's
+    stored full-size values; raises on a mismatch.  Returns the checked keys."""
+    checked = []
+    for (k, o, m, c, s) in per_call:
+        e = golden.get("k=%d %s" % (k, o))
+        if not e:
+            continue
+        if c != e["count"]:
+            raise AssertionError("k=%d %s %s: count %d, oracle %d" % (k, o, m, c, e["count"]))
+        checked.append("k=%d %s %s count" % (k, o, m))
+        if s is not None and "checksum" in e:
+            if s != e["checksum"]:
+                raise AssertionError("k=%d %s: checksum %#x, oracle %#x" % (k, o, s, e["checksum"]))
+            checked.append("k=%d %s %s checksum" % (k, o, m))
+    return sorted(set(checked))
+
+
 def run_ours(args, rank, world):
     import numpy as np
     import torch
@@ -118,6 +151,8 @@ def run_ours(args, rank, world):
     stream = torch.cuda.current_stream()
     rp, col = workload()
     n, nnz = len(rp) - 1, len(col)
+    golden = _load_work()
+    peaks = kcl.kcl_measure_int_peaks()
     g = kcl.kcl_load_csr(rp, col)
     # the library's autotuner picks, per out-degree class, SDegree's
     # bitmap-versus-list threshold and leaf form and both paths' warps per
@@ -129,29 +164,38 @@ def run_ours(args, rank, world):
     kcl.kcl_enable_timing(g, True)
 
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.int32, device="cuda")
+    ring = torch.empty(RING_BYTES // 4, dtype=torch.int32, device="cuda")
 
-    def step(graph, collect=None):
+    def step(graph, collect=None, results=None):
         total = 0
         for k, o, mode in STEP_PLAN:
+            s = None
             if mode == "count":
                 c = kcl.kcl_count(graph, k, o)
             else:
-                c, s, _, _ = kcl.kcl_list(graph, k, o, None)
+                r = ring[: (ring.numel() // k) * k]
+                c, s, w, _ = kcl.kcl_list(graph, k, o, r, wrap=True)
+                assert w == min(c, r.numel() // k)
             total += c
+            if results is not None:
+                results.append((k, o, mode, c, s))
             if collect is not None:
                 ms, la, cl = kcl.kcl_last_timing(graph)
                 collect.append((k, o, mode, c, ms, la, cl))
         return total
 
-    for _ in range(args.warmup):
-        step(g)
+    for i in range(args.warmup):
+        res0 = []
+        step(g, results=res0)
+        if i == 0:
+            checked = check_golden(res0, golden)
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
 
     clocks = ClockSampler(dev)
     clocks.start()
-    per_call = []
+    per_call, results = [], []
     dev_ms = 0.0
     cliques = 0
     for _ in range(args.steps):
@@ -159,18 +203,34 @@ def run_ours(args, rank, world):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
         e0.record(stream)
-        cliques += step(g, per_call)
+        cliques += step(g, per_call, results)
         e1.record(stream)
         e1.synchronize()
         dev_ms += e0.elapsed_time(e1)
     torch.cuda.synchronize()
+    # k = 6 in both orderings, one timed call each (seconds per call)
+    k6 = {}
+    if not args.no_k6:
+        for k, o, _ in K6_PLAN:
+            flush.fill_(1)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            c = kcl.kcl_count(g, k, o)
+            e1.record(stream)
+            e1.synchronize()
+            ms, la, cl = kcl.kcl_last_timing(g)
+            k6[o] = {"count": c, "ms": e0.elapsed_time(e1), "listing_ms": ms["listing"],
+                     "classes": [[x["lo"], x["hi"], x["roots"], round(x["ms"], 2)] for x in cl
+                                 if x["roots"]]}
     clk = clocks.stop()
+    check_golden(results, golden)
 
     # e2e: pinned host CSR -> C ABI (copy, validate, all calls) -> counts back
     rp_pin = torch.from_numpy(rp.view(np.int64)).pin_memory()
     col_pin = torch.from_numpy(col.view(np.int32)).pin_memory()
     e2e_ms = 0.0
-    e2e_steps = max(1, min(args.steps, 2))
+    e2e_steps = max(1, min(args.steps, 3))
     for _ in range(e2e_steps):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -188,7 +248,8 @@ def run_ours(args, rank, world):
     value = cliques_all / (dev_ms / 1e3)
     e2e_value = (cliques // args.steps) * e2e_steps * world / (e2e_ms / 1e3)
 
-    roof = roofline(per_call, args.steps)
+    sm_mhz = clk.get("sm_mhz") or peaks["sm_clock_mhz"]
+    roof = roofline(per_call, args.steps, peaks, sm_mhz)
     launches = sum(sum(pc[5].values()) - pc[5]["total"] for pc in per_call) // args.steps
     res = {
         "metric": METRIC, "value": value, "unit": "k-cliques/s", "n_gpus": world,
@@ -197,19 +258,29 @@ def run_ours(args, rank, world):
         "data": "synthetic (seeded R-MAT generator, no dataset)",
         "config": {"workload": "rmat-scale20-ef16", "n": n, "undirected_edges": nnz // 2,
                    "plan": ["k=%d %s %s" % p for p in STEP_PLAN],
+                   "listing_ring": "%d GiB device ring, wrap=1, k uint32 ids per clique" %
+                                   (RING_BYTES >> 30),
                    "l2": "inputs (%.0f MB CSR) larger than L2; L2 also flushed between steps"
                          % ((n + 1) * 8 / 1e6 + nnz * 4 / 1e6),
                    "parallelism": "replicas" if world > 1 else "single-gpu",
                    "tuning": tuning},
         "counts": {"k=%d %s %s" % pc[:3]: pc[3] for pc in per_call[: len(STEP_PLAN)]},
+        "oracle_checked": checked,
         "e2e": {"value": e2e_value, "unit": "k-cliques/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
         "clocks": clk,
         "roofline": roof,
-        "roofline_counting": roofline(per_call, args.steps, modes=("count",)),
+        "roofline_counting": roofline(per_call, args.steps, peaks, sm_mhz, modes=("count",)),
+        "roofline_listing": roofline(per_call, args.steps, peaks, sm_mhz, modes=("list",)),
+        "roofline_frontend": frontend_roofline(per_call, args.steps, n, nnz),
+        "int_peaks": peaks,
         "stage_ms": stage_summary(per_call, args.steps),
     }
+    if k6:
+        tot = sum(v["count"] for v in k6.values())
+        res["c2_k6"] = {"orderings": k6, "orderings_agree": len({v["count"] for v in k6.values()}) == 1,
+                        "k_cliques_per_s": tot / (sum(v["ms"] for v in k6.values()) / 1e3)}
     g.free()
     return res
 
@@ -247,22 +318,23 @@ def stage_summary(per_call, steps):
     return res
 
 
-def roofline(per_call, steps, modes=("count", "list")):
+def roofline(per_call, steps, peaks, sm_mhz, modes=("count", "list")):
     """The dominant kernel: the single listing launch with the largest device
     time per step -- one out-degree class of the call family (among `modes`)
     whose listing stage is longest.  Its bound is the integer pipe; the peak
-    is derived from the SM count and clock:
-      counting, BitCol: one AND + POPC per bitmap word, 16 POPC per SM and
-        clock; unit = BitJoin words (Algorithm 6);
-      counting, SDegree: at least one compare per merge element, 64 compares
-        per SM and clock; unit = merge elements (Lemma 2);
-      listing (checksum, no ring): k SplitMix64 rounds per clique, each two
-        64-bit multiplies of three 32-bit IMADs, 64 IMADs per SM and clock;
-        unit = cliques.
-    `achieved` = the oracle's algorithmic work (or clique count) for the roots
-    of that class (tests/golden/rmat20_work.json, split by out-degree) / that
-    launch's CUDA-event time."""
-    peaks, src = _peaks()
+    is the measured per-SM rate of its unit (kcl_measure_int_peaks) x SMs x
+    the SM clock sampled during the timed region:
+      counting, BitCol: BitJoin words of Algorithm 6 (a 32-bit word of a
+        bit-row ANDed with the candidate set and counted), peak = the
+        measured BitJoin word rate;
+      counting, SDegree: the merge joins of Algorithm 5 each costed at the
+        width of a bitmap over the root's out-neighbourhood, ceil(d+/32)
+        words (what the bit-row form computes), same peak;
+      listing: cliques, each k SplitMix64 rounds of the checksum, peak = the
+        measured round rate / k.
+    `achieved` = the oracle's count of that unit for the roots of that class
+    (tests/golden/rmat20_work.json, split by out-degree) / that launch's
+    CUDA-event time."""
     work = _load_work()
     fam = {}
     for (k, o, m, c, ms, la, cl) in per_call:
@@ -272,31 +344,68 @@ def roofline(per_call, steps, modes=("count", "list")):
         f["listing"].append(ms["listing"])
         for ci, cc in enumerate(cl):
             f["classes"].setdefault((ci, cc["lo"], cc["hi"], cc["roots"]), []).append(cc["ms"])
+    if not fam:
+        return None
     (k, o, m), f = max(fam.items(), key=lambda kv: sum(kv[1]["listing"]))
     (ci, lo, hi, roots), times = max(f["classes"].items(), key=lambda kv: sum(kv[1]))
     avg_ms = sum(times) / len(times)
-    sm_mhz = peaks.get("sm_max_mhz", 2070.0)
     entry = work.get("k=%d %s" % (k, o))
+    sms = peaks["num_sms"]
     if m == "list":
-        per_clk, what, unit = 64.0 / (6 * k), "64 IMAD/clk / (6 k IMAD per clique)", "Gclique/s"
+        per_clk = peaks["mix64_per_sm_clk"] / k
+        what, unit = "%.2f SplitMix64 rounds/clk/SM / %d per clique" % (peaks["mix64_per_sm_clk"], k), \
+            "Gclique/s"
         wk = class_work(entry, lo, hi, field="count_by_outdeg")
     else:
-        per_clk = 16 if o == "color" else 64
-        what = "16 POPC/clk" if o == "color" else "64 compares/clk"
-        unit = "Gword/s" if o == "color" else "Gelem/s"
-        wk = class_work(entry, lo, hi)
-    peak_gops = 152 * per_clk * sm_mhz * 1e6 / 1e9
+        per_clk = peaks["bitjoin_words_per_sm_clk"]
+        what = "%.2f BitJoin words/clk/SM" % per_clk
+        unit = "Gword/s"
+        wk = class_work(entry, lo, hi, field="work_by_outdeg" if o == "color" else "bitrow_words_by_outdeg")
+    peak_g = sms * per_clk * sm_mhz * 1e6 / 1e9
     achieved = (wk / (avg_ms / 1e3) / 1e9) if wk else None
     kern = KERNEL_NAMES.get((o, m, ci), "listing launch of class %d" % ci)
     tr = TRAFFIC.get((k, o, m, ci))
     return {"kernel": "%s (k=%d %s %s, roots with %d <= d+ <= %d)" % (kern, k, o, m, lo, hi),
-            "bound": "alu", "achieved": achieved, "peak": peak_gops, "unit": unit,
-            "frac": (achieved / peak_gops) if achieved else None,
+            "bound": "alu", "achieved": achieved, "peak": peak_g, "unit": unit,
+            "frac": (achieved / peak_g) if achieved else None,
             "traffic": tr[0] if tr else None,
             "traffic_source": tr[1] if tr else None,
             "work_per_launch": wk, "roots": roots, "avg_ms": avg_ms,
             "listing_stage_ms": sum(f["listing"]) / len(f["listing"]),
-            "peak_source": "derived: 152 SMs x %s x %.0f MHz (%s clock)" % (what, sm_mhz, src)}
+            "peak_source": "measured: %d SMs x %s (kcl_measure_int_peaks) x %.0f MHz (sampled SM clock)"
+                           % (sms, what, sm_mhz)}
+
+
+def frontend_roofline(per_call, steps, n, nnz):
+    """The front-end passes of the k = 4 counting calls against the measured
+    HBM copy bandwidth.  Algorithmic bytes per pass (n vertices, nnz CSR
+    entries, C = 8 (n + 1) + 4 nnz bytes of CSR):
+      pre_core: read the row offsets, write alive + degrees: 8 (n + 1) + 5 n;
+      pre_list: one pass over the CSR and alive: C + n;
+      orientation, degree: two passes over the CSR, alive and keys (out-degree
+        count, then fill) + the out-CSR written: 2 (C + 5 n) + 4 (n + 1) + 2 nnz;
+      orientation, colour: the same + the peel's pass over the CSR and its
+        degree/key arrays: 3 (C + 5 n) + 4 (n + 1) + 2 nnz."""
+    peaks, src = _peaks()
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    C = 8 * (n + 1) + 4 * nnz
+    out = {}
+    for o in ("color", "degree"):
+        fam = [pc for pc in per_call if pc[0] == 4 and pc[1] == o and pc[2] == "count"]
+        if not fam:
+            continue
+        ms = {st: sum(pc[4][st] for pc in fam) / len(fam) for st in ("pre_core", "pre_list", "orientation")}
+        passes = 3 if o == "color" else 2
+        byt = {"pre_core": 8 * (n + 1) + 5 * n, "pre_list": C + n,
+               "orientation": passes * (C + 5 * n) + 4 * (n + 1) + 2 * nnz}
+        out["k=4 %s count" % o] = {
+            st: {"bytes": byt[st], "ms": round(ms[st], 3),
+                 "GB_s": byt[st] / (ms[st] / 1e3) / 1e9 if ms[st] > 0 else None,
+                 "frac": (byt[st] / (ms[st] / 1e3) / 1e9 / hbm) if ms[st] > 0 else None}
+            for st in byt}
+    out["peak_GB_s"] = hbm
+    out["peak_source"] = "%s HBM copy bandwidth (MEASURED_PEAKS.json)" % src
+    return out
 
 
 # listing kernels of the out-degree classes (count mode), by (ordering, mode,
@@ -333,10 +442,7 @@ KERNEL_NAMES = {
 # names the summary under profiles/.  An entry is removed when its kernel
 # changes, until a new capture exists.
 _DRAM = "profiles/dram_listing_kernels_rmat20.md"
-TRAFFIC = {
-    (4, "color", "list", 4): (31.20e6, _DRAM),
-    (4, "color", "list", 5): (13.73e6, _DRAM),
-}
+TRAFFIC = {}
 
 
 def class_work(entry, lo, hi, field="work_by_outdeg"):
@@ -366,47 +472,101 @@ def _load_work():
 
 
 # --------------------------------------------------------- oracle (CPU)
-def oracle_sample(budget_s=15.0):
-    """Time the oracle on a bounded sample of the workload: every 97th root
-    of the degeneracy DAG (BitCol) and of the degree DAG (SDegree), k = 4."""
+_GRAPH = None
+
+
+def _oracle_task(task):
+    """One call of STEP_PLAN by the oracle on a subset of the roots (the
+    oracle as it stands: its own Pre-Core, Pre-List and orientation over the
+    whole graph, then the roots given).  Counting calls use its count-only
+    mode, listing calls enumerate and hash every clique."""
+    global _GRAPH
     import numpy as np
 
     import oracle
-    rp, col = workload()
-    n = len(rp) - 1
-    roots = np.arange(0, n, 97, dtype=np.uint32)
-    t0 = time.perf_counter()
-    found = 0
-    calls = 0
-    for fn in (oracle.bitcol, oracle.sdegree):
-        r = fn(rp, col, 4, roots=roots)
-        found += r["count"]
-        calls += 1
-        if time.perf_counter() - t0 > budget_s:
-            break
-    dt = time.perf_counter() - t0
-    return {"value": found / dt, "unit": "k-cliques/s", "cores": 1, "kind": "oracle",
-            "sample": "k=4, roots 0,97,194,... (%d of %d) of R-MAT scale 20; %d ordering(s); "
-                      "includes the oracle's full Pre-Core/Pre-List/orientation passes" %
-                      (len(roots), n, calls), "seconds": dt}
+    k, o, mode, roots = task
+    if _GRAPH is None:
+        _GRAPH = workload()
+    rp, col = _GRAPH
+    fn = oracle.bitcol if o == "color" else oracle.sdegree
+    kw = {"L": 32} if o == "color" else {}
+    t = time.perf_counter()
+    r = fn(rp, col, k, roots=np.asarray(roots, np.uint32), count_only=(mode == "count"), **kw)
+    return r["count"], time.perf_counter() - t
+
+
+def _plan_tasks(stride, shards):
+    n = 1 << SCALE
+    tasks = []
+    for k, o, mode in STEP_PLAN:
+        roots = list(range(0, n, stride))
+        tasks += [(k, o, mode, roots[i::shards]) for i in range(shards)]
+    return tasks, len(range(0, n, stride))
+
+
+def oracle_plan_sample(stride, pool=None, procs=1):
+    """The oracle on every call of STEP_PLAN, restricted to roots 0, stride,
+    2 stride, ...: sequentially in this process (pool None), or sharded over
+    a spawn pool of `procs` processes.  Returns (cliques, seconds, calls)."""
+    if pool is None:
+        tasks, nr = _plan_tasks(stride, 1)
+        t = time.perf_counter()
+        found = sum(_oracle_task(tk)[0] for tk in tasks)
+        return found, time.perf_counter() - t, nr
+    shards = max(1, -(-procs // len(STEP_PLAN)))
+    tasks, nr = _plan_tasks(stride, shards)
+    t = time.perf_counter()
+    found = sum(c for c, _ in pool.imap_unordered(_oracle_task, tasks))
+    return found, time.perf_counter() - t, nr
+
+
+def _oracle_pool(procs):
+    import multiprocessing as mp
+    return mp.get_context("spawn").Pool(procs)  # spawned: safe after CUDA use
+
+
+CPU_STRIDE = 997
+
+
+def oracle_sample():
+    """cpu_baseline of the main line: the same plan as the GPU step on every
+    997th root, single-threaded and on all host cores (spawned processes)."""
+    procs = os.cpu_count() or 1
+    one = oracle_plan_sample(CPU_STRIDE)
+    with _oracle_pool(procs) as pool:
+        oracle_plan_sample(CPU_STRIDE * 7, pool, procs)  # start-up (imports, graph) untimed
+        allc = oracle_plan_sample(CPU_STRIDE, pool, procs)
+    sample = ("the %d step calls (%s) on roots 0, %d, 2*%d, ... (%d of %d) of R-MAT scale 20; "
+              "count-only mode for counting calls, every clique hashed for listing calls; "
+              "each call includes the oracle's own Pre-Core/Pre-List/orientation pass"
+              % (len(STEP_PLAN), ", ".join("k=%d %s %s" % p for p in STEP_PLAN), CPU_STRIDE,
+                 CPU_STRIDE, one[2], 1 << SCALE))
+    return {"value": allc[0] / allc[1], "unit": "k-cliques/s", "cores": procs, "kind": "oracle",
+            "sample": sample, "seconds": allc[1],
+            "single_thread": {"value": one[0] / one[1], "cores": 1, "seconds": one[1]},
+            "nproc": procs}
 
 
 def run_reference(args, rank, world):
     if rank != 0:
         return None
+    procs = os.cpu_count() or 1
     vals = []
-    for _ in range(args.warmup + args.steps):
-        vals.append(oracle_sample(budget_s=10.0))
+    with _oracle_pool(procs) as pool:
+        for _ in range(args.warmup + args.steps):
+            vals.append(oracle_plan_sample(2 * CPU_STRIDE + 1, pool, procs))
     timed = vals[args.warmup:]
-    value = sum(v["value"] for v in timed) / len(timed)
-    sec = sum(v["seconds"] for v in timed)
-    cb = dict(timed[-1])
-    cb["value"] = value
+    found = sum(v[0] for v in timed)
+    sec = sum(v[1] for v in timed)
+    value = found / sec
+    sample = ("the %d step calls on roots 0, %d, ... (%d of %d) of R-MAT scale 20, sharded over %d "
+              "spawned processes" % (len(STEP_PLAN), 2 * CPU_STRIDE + 1, timed[0][2], 1 << SCALE, procs))
+    cb = {"value": value, "unit": "k-cliques/s", "cores": procs, "kind": "oracle", "sample": sample}
     return {"impl": "reference", "metric": METRIC, "value": value, "unit": "k-cliques/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": sec * 1e3 / len(timed), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u32/u64", "data": "synthetic (seeded R-MAT generator)",
-            "config": {"workload": "rmat-scale20-ef16", "sample": cb["sample"]},
+            "config": {"workload": "rmat-scale20-ef16", "sample": sample},
             "cpu_baseline": cb,
             "e2e": {"value": value, "unit": "k-cliques/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
@@ -629,8 +789,10 @@ def profile_case(spec):
     g = kcl.kcl_load_csr(rp, col)
     if mode == "count":
         print(kcl.kcl_count(g, k, ordering))
-    else:
-        print(kcl.kcl_list(g, k, ordering, None))
+    else:  # into a wrapping device ring, as the bench's listing calls
+        import torch
+        ring = torch.empty(RING_BYTES // 4 // k * k, dtype=torch.int32, device="cuda")
+        print(kcl.kcl_list(g, k, ordering, ring, wrap=True))
     g.free()
 
 
@@ -641,6 +803,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-k6", action="store_true", help="skip the timed k = 6 calls")
     ap.add_argument("--form", default="single", choices=["single", "batch", "serve", "ablation"],
                     help="single: the R-MAT scale-20 line; batch / serve: the batched and "
                          "served workloads, each printing its own JSON line")

@@ -41,6 +41,7 @@ class Counters(ctypes.Structure):
         ("build_reads", ctypes.c_uint64),
         ("roots", ctypes.c_uint64),
         ("max_outdeg", ctypes.c_uint64),
+        ("bitrow_words", ctypes.c_uint64),
     ]
 
     def as_dict(self):

@@ -81,6 +81,8 @@ typedef struct {
     uint64_t build_reads;    /* BitCol: sum over v in N+_u of d+_v (G_u construction) */
     uint64_t roots;          /* roots with d+_u >= k-1 that were expanded */
     uint64_t max_outdeg;     /* maximum out-degree of the DAG (Delta) */
+    uint64_t bitrow_words;   /* SDegree: per merge join, ceil(d+_root / 32) -- the words a
+                                bitmap over N+_root's index space touches for it */
 } oracle_counters;
 
 /* -------------------------------------------------------- clique sink */
@@ -505,6 +507,7 @@ typedef struct {
     uint32_t k;
     uint32_t R[64];
     uint32_t **buf;
+    uint32_t nw_root;      /* ceil(d+_root / 32) of the current root */
     uint32_t *trace;       /* optional call trace: [l, |R|, R..., |C|, C...] per call */
     uint64_t trace_cap, trace_len;
 } sdeg_ctx;
@@ -531,6 +534,7 @@ static void sdegree_list(sdeg_ctx *c, uint32_t l, uint32_t nR, const uint32_t *C
         uint32_t np = merge_intersect(c->D->oadj + c->D->optr[u], du, C, nC, Cp);
         c->cnt->intersections++;
         c->cnt->merge_elems += (uint64_t)nC + du;
+        c->cnt->bitrow_words += c->nw_root;
         if (l == 2) {
             c->R[nR] = u;
             if (c->S->count_only) sink_add(c->S, np);
@@ -586,6 +590,7 @@ int oracle_sdegree(uint32_t n, const uint64_t *rp, const uint32_t *col, uint32_t
         if (!P.alive[u] || du < k - 1) continue;
         counters->roots++;
         c.R[0] = u; S.root = u;
+        c.nw_root = (du + 31) / 32;
         sdegree_list(&c, k - 1, 1, D.oadj + D.optr[u], du);
     }
     for (uint32_t i = 0; c.buf && i <= k; i++) free(c.buf[i]);

@@ -379,11 +379,15 @@ __device__ void leaf_batch(const View &v, const uint32_t *C, uint32_t cw, const 
     if (!tot) return;
     unsigned long long slot0 = 0;
     if (em.ring) {
-        if (lane == 0) slot0 = atomicAdd(&res->emitted, (unsigned long long)tot);
+        if (lane == 0) slot0 = ring_base(atomicAdd(&res->emitted, (unsigned long long)tot), em.capacity, em.wrap);
         slot0 = __shfl_sync(kFull, slot0, 0);
     }
-    const uint32_t run = (tot + 31) >> 5;
-    const uint32_t r0 = lane * run;
+    // balanced runs: lane i takes tot/32 cliques, one more when i < tot%32;
+    // its j-th clique goes to record j * 32 + i of the batch, so the warp's
+    // stores at each step are 32 consecutive records
+    const uint32_t rq = tot >> 5, rrem = tot & 31u;
+    const uint32_t r0 = lane * rq + (lane < rrem ? lane : rrem);
+    const uint32_t rlen = rq + (lane < rrem ? 1u : 0u);
     uint32_t o = 0;  // number of lanes whose inclusive prefix is <= r0
 #pragma unroll
     for (uint32_t step = 16; step > 0; step >>= 1) {
@@ -391,8 +395,8 @@ __device__ void leaf_batch(const View &v, const uint32_t *C, uint32_t cw, const 
         if (vv <= r0) o += step;
     }
     const uint32_t eo = __shfl_sync(kFull, excl, o & 31u);
-    if (r0 >= tot) return;
-    const uint32_t r1 = r0 + run < tot ? r0 + run : tot;
+    if (rlen == 0) return;
+    const uint32_t r1 = r0 + rlen;
     const uint64_t seed = hash_seed(v.k);
     uint32_t po = q[o];
     const uint32_t *row = v.B + po * v.WP;
@@ -410,7 +414,7 @@ __device__ void leaf_batch(const View &v, const uint32_t *C, uint32_t cw, const 
         // mm holds the remaining bits of word t (its lowest is clique r)
         const uint32_t b = t * 32 + (__ffs(mm) - 1);
         cks += clique_hash2(sortedR, v.k - 2, a, v.ids[b], seed,
-                            ring_slot(em.ring, em.capacity, em.wrap, slot0 + r, v.k));
+                            ring_rec(em.ring, em.capacity, em.wrap, slot0, (r - r0) * 32 + lane, v.k));
         mm &= mm - 1;
         while (!mm && r + 1 < r1) {
             if (++t >= wl) {  // next candidate with cliques

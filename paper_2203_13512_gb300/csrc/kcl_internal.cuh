@@ -161,13 +161,28 @@ __device__ __forceinline__ uint64_t clique_hash2(const uint32_t *sortedR, uint32
     return h;
 }
 
-// Ring slot of a clique (null when it does not fit and the ring does not wrap).
-__device__ __forceinline__ uint32_t *ring_slot(uint32_t *ring, unsigned long long capacity, int wrap,
-                                               unsigned long long slot, uint32_t k) {
+// Ring records of a batch: the batch claims `count` consecutive record
+// indices from `emitted` (one atomic), and its first index becomes the base
+// of ring_rec -- taken mod capacity once per batch when the ring wraps, so
+// no clique pays a 64-bit division.
+__device__ __forceinline__ unsigned long long ring_base(unsigned long long first,
+                                                        unsigned long long capacity, int wrap) {
+    return wrap ? first % capacity : first;
+}
+
+// Record `off` of a batch whose base is `base` (null when it does not fit
+// and the ring does not wrap).
+__device__ __forceinline__ uint32_t *ring_rec(uint32_t *ring, unsigned long long capacity, int wrap,
+                                              unsigned long long base, uint32_t off, uint32_t k) {
     if (!ring) return nullptr;
-    if (wrap) slot %= capacity;
-    else if (slot >= capacity) return nullptr;
-    return ring + slot * k;
+    unsigned long long s = base + off;
+    if (wrap) {
+        if (s >= capacity) s -= capacity;
+        if (s >= capacity) s %= capacity;  // only for rings smaller than a batch
+    } else if (s >= capacity) {
+        return nullptr;
+    }
+    return ring + s * k;
 }
 
 // Inclusive prefix sum over the 32 lanes of a warp (all lanes active).

@@ -62,7 +62,8 @@ __device__ void emit_matches(bool found, uint32_t w, uint32_t v, uint32_t k, con
     if (!m) return;
     unsigned long long slot0 = 0;
     if (em.ring) {
-        if (lane == 0) slot0 = atomicAdd(&res->emitted, (unsigned long long)__popc(m));
+        if (lane == 0)
+            slot0 = ring_base(atomicAdd(&res->emitted, (unsigned long long)__popc(m)), em.capacity, em.wrap);
         slot0 = __shfl_sync(kFull, slot0, 0);
     }
     if (!found) return;
@@ -70,8 +71,8 @@ __device__ void emit_matches(bool found, uint32_t w, uint32_t v, uint32_t k, con
         v = em.idmap[v];
         w = em.idmap[w];
     }
-    const unsigned long long sl = slot0 + __popc(m & ((1u << lane) - 1u));
-    cks += clique_hash2(sortedR, k - 2, v, w, hash_seed(k), ring_slot(em.ring, em.capacity, em.wrap, sl, k));
+    cks += clique_hash2(sortedR, k - 2, v, w, hash_seed(k),
+                        ring_rec(em.ring, em.capacity, em.wrap, slot0, __popc(m & ((1u << lane) - 1u)), k));
 }
 
 // C' = N+_v intersect C; writes C' (ascending) to `out` when non-null and
@@ -368,14 +369,14 @@ __device__ void flush_pairs(const LView &v, uint32_t nb, const LStack &st, const
     __syncwarp();
     unsigned long long slot0 = 0;
     if (em.ring) {
-        if (lane == 0) slot0 = atomicAdd(&res->emitted, (unsigned long long)nb);
+        if (lane == 0) slot0 = ring_base(atomicAdd(&res->emitted, (unsigned long long)nb), em.capacity, em.wrap);
         slot0 = __shfl_sync(kFull, slot0, 0);
     }
     const uint64_t seed = hash_seed(k);
     for (uint32_t e = lane; e < nb; e += 32) {
         const uint32_t pr = st.ebuf[e];
         cks += clique_hash2(st.sortedR, k - 2, v.nbr[pr >> 16], v.nbr[pr & 0xFFFFu], seed,
-                            ring_slot(em.ring, em.capacity, em.wrap, slot0 + e, k));
+                            ring_rec(em.ring, em.capacity, em.wrap, slot0, e, k));
     }
     __syncwarp();
 }
@@ -613,11 +614,15 @@ __device__ void bleaf_batch(const BView &v, const uint32_t *C, const uint16_t *q
     if (!tot) return;
     unsigned long long slot0 = 0;
     if (em.ring) {
-        if (lane == 0) slot0 = atomicAdd(&res->emitted, (unsigned long long)tot);
+        if (lane == 0) slot0 = ring_base(atomicAdd(&res->emitted, (unsigned long long)tot), em.capacity, em.wrap);
         slot0 = __shfl_sync(kFull, slot0, 0);
     }
-    const uint32_t run = (tot + 31) >> 5;
-    const uint32_t r0 = lane * run;
+    // balanced runs: lane i takes tot/32 cliques, one more when i < tot%32;
+    // its j-th clique goes to record j * 32 + i of the batch, so the warp's
+    // stores at each step are 32 consecutive records
+    const uint32_t rq = tot >> 5, rrem = tot & 31u;
+    const uint32_t r0 = lane * rq + (lane < rrem ? lane : rrem);
+    const uint32_t rlen = rq + (lane < rrem ? 1u : 0u);
     uint32_t o = 0;
 #pragma unroll
     for (uint32_t step = 16; step > 0; step >>= 1) {
@@ -625,8 +630,8 @@ __device__ void bleaf_batch(const BView &v, const uint32_t *C, const uint16_t *q
         if (vv <= r0) o += step;
     }
     const uint32_t eo = __shfl_sync(kFull, excl, o & 31u);
-    if (r0 >= tot) return;
-    const uint32_t r1 = r0 + run < tot ? r0 + run : tot;
+    if (rlen == 0) return;
+    const uint32_t r1 = r0 + rlen;
     const uint32_t k = v.k;
     const uint64_t seed = hash_seed(k);
     uint32_t qo = q[o];
@@ -643,7 +648,7 @@ __device__ void bleaf_batch(const BView &v, const uint32_t *C, const uint16_t *q
     for (uint32_t r = r0; r < r1; r++) {
         const uint32_t b = t * 32 + (__ffs(mm) - 1);
         cks += clique_hash2(sortedR, k - 2, a, v.ids[b], seed,
-                            ring_slot(em.ring, em.capacity, em.wrap, slot0 + r, k));
+                            ring_rec(em.ring, em.capacity, em.wrap, slot0, (r - r0) * 32 + lane, k));
         mm &= mm - 1;
         while (!mm && r + 1 < r1) {
             if (++t >= v.W) {  // next candidate with cliques

@@ -12,6 +12,9 @@ oracle's count-only mode gives:
             number of expanded roots and the k-cliques they list, split by
             the root's out-degree d+_u in power-of-two buckets: key "b" holds
             the roots with 2^(b-1) < d+_u <= 2^b.
+  bitrow_words_by_outdeg (SDegree) -- per bucket, the merge joins of
+            Algorithm 5 each costed at ceil(d+_root / 32) words: the words a
+            bitmap over the root's out-neighbourhood touches per join.
 The roots are split into buckets (and each bucket into interleaved shards)
 so that the oracle runs on every core; the count adds the Pre-List cliques
 (Algorithm 4), which the per-root runs leave out.
@@ -25,7 +28,8 @@ so that the oracle runs on every core; the count adds the Pre-List cliques
   out-degree bucket (numpy default_rng(1000 + k)) -- stored as
   "sample": {"roots": [...], "per_root": [...]} for a (k, ordering) whose
   full count is beyond the oracle.
-Usage: python tests/golden/make_rmat20_work.py [--checksum | --sample] [k ...]
+Usage: python tests/golden/make_rmat20_work.py [--checksum | --sample | --color | --degree] [k ...]
+(--color / --degree: counts and work of that ordering only.)
 """
 import json
 import multiprocessing as mp
@@ -79,6 +83,7 @@ def one(task):
         r = oracle.sdegree(rp, col, k, roots=roots, count_only=True)
         work = r["counters"]["merge_elems"]
     return (k, ordering), bucket, r["count"], work, r["counters"]
+
 
 
 def one_checksum(task):
@@ -190,8 +195,12 @@ def main():
         return main_checksum([int(a) for a in args[1:]] or [4])
     if args and args[0] == "--sample":
         return main_sample([int(a) for a in args[1:]] or [6])
+    orderings = ("color", "degree")
+    if args and args[0] in ("--color", "--degree"):
+        orderings = (args[0][2:],)
+        args = args[1:]
     ks = [int(a) for a in args] or [4, 5]
-    jobs = [(k, o) for k in ks for o in ("color", "degree")]
+    jobs = [(k, o) for k in ks for o in orderings]
     data = {}
     if os.path.exists(OUT):
         with open(OUT) as f:
@@ -220,12 +229,22 @@ def main():
             a["work_by_outdeg"][key] = a["work_by_outdeg"].get(key, 0) + work
             a["roots_by_outdeg"][key] = a["roots_by_outdeg"].get(key, 0) + ctr["roots"]
             a["count_by_outdeg"][key] = a["count_by_outdeg"].get(key, 0) + cnt
+            if job[1] == "degree":
+                bw = a.setdefault("bitrow_words_by_outdeg", {})
+                bw[key] = bw.get(key, 0) + ctr["bitrow_words"]
             left[job] -= 1
             if left[job] == 0:
                 a["oracle_wall_seconds"] = round(time.time() - t0, 1)
                 a["work_by_outdeg"] = dict(sorted(a["work_by_outdeg"].items(), key=lambda x: int(x[0])))
                 a["roots_by_outdeg"] = dict(sorted(a["roots_by_outdeg"].items(), key=lambda x: int(x[0])))
                 a["count_by_outdeg"] = dict(sorted(a["count_by_outdeg"].items(), key=lambda x: int(x[0])))
+                if "bitrow_words_by_outdeg" in a:
+                    a["bitrow_words_by_outdeg"] = dict(sorted(a["bitrow_words_by_outdeg"].items(),
+                                                              key=lambda x: int(x[0])))
+                old = data.get("k=%d %s" % job, {})
+                for keep in ("checksum", "sample"):  # written by the other modes
+                    if keep in old:
+                        a[keep] = old[keep]
                 data["k=%d %s" % job] = a
                 print("k=%d %s" % job, a, flush=True)
                 with open(OUT, "w") as f:

@@ -30,22 +30,25 @@ def _call(k, o, m, listing_ms, classes):
     return (k, o, m, 0, ms, la, cl)
 
 
+PEAKS = {"num_sms": 152, "sm_clock_mhz": 2070.0, "bitjoin_words_per_sm_clk": 15.7,
+         "mix64_per_sm_clk": 3.9}
+
+
 def test_roofline_picks_the_longest_launch(monkeypatch):
-    work = {"k=5 degree": {"work": 300, "work_by_outdeg": {"5": 100, "9": 200}},
+    work = {"k=5 degree": {"work": 300, "bitrow_words_by_outdeg": {"5": 100, "9": 200}},
             "k=5 color": {"work": 50, "work_by_outdeg": {"5": 50}}}
     monkeypatch.setattr(bench, "_load_work", lambda: work)
     calls = [_call(5, "color", "count", 10.0, [(4, 32, 10, 10.0)]),
              _call(5, "degree", "count", 30.0, [(4, 32, 10, 5.0), (257, 512, 3, 25.0)])] * 2
-    r = bench.roofline(calls, 2)
-    assert r["bound"] == "alu" and r["unit"] == "Gelem/s"
+    r = bench.roofline(calls, 2, PEAKS, 2000.0)
+    assert r["bound"] == "alu" and r["unit"] == "Gword/s"
     assert "257 <= d+ <= 512" in r["kernel"]
     assert r["work_per_launch"] == 200 and r["avg_ms"] == 25.0
     assert abs(r["achieved"] - 200 / 25e-3 / 1e9) < 1e-12
     assert abs(r["frac"] - r["achieved"] / r["peak"]) < 1e-12
-    # SDegree's peak counts 64 compares per SM and clock, BitCol's 16 POPC
-    calls = [_call(5, "color", "count", 30.0, [(4, 32, 10, 30.0)])]
-    rc = bench.roofline(calls, 1)
-    assert abs(r["peak"] / rc["peak"] - 4.0) < 1e-12
+    # measured BitJoin word rate x SMs x sampled clock
+    assert abs(r["peak"] - 152 * 15.7 * 2000e6 / 1e9) < 1e-9
+    assert "measured" in r["peak_source"]
 
 
 def test_roofline_listing_counts_cliques(monkeypatch):
@@ -54,12 +57,34 @@ def test_roofline_listing_counts_cliques(monkeypatch):
     monkeypatch.setattr(bench, "_load_work", lambda: work)
     calls = [_call(4, "color", "list", 40.0, [(3, 32, 10, 10.0), (257, 512, 3, 30.0)]),
              _call(4, "color", "count", 5.0, [(3, 32, 10, 5.0)])]
-    r = bench.roofline(calls, 1)
+    r = bench.roofline(calls, 1, PEAKS, 2070.0)
     assert r["unit"] == "Gclique/s" and r["work_per_launch"] == 9000
-    # k SplitMix64 rounds per clique at 6 IMADs each, 64 IMADs per SM and clock
-    assert abs(r["peak"] - 152 * 64 / 24 * 2070e6 / 1e9) < 1e-6
-    rc = bench.roofline(calls, 1, modes=("count",))
-    assert rc["unit"] == "Gword/s" and rc["work_per_launch"] == 50
+    # k SplitMix64 rounds per clique at the measured round rate
+    assert abs(r["peak"] - 152 * 3.9 / 4 * 2070e6 / 1e9) < 1e-9
+    assert bench.roofline(calls, 1, PEAKS, 2070.0, modes=("nothing",)) is None
+
+
+def test_frontend_roofline_bytes():
+    calls = [_call(4, "color", "count", 5.0, [(3, 32, 10, 5.0)]),
+             _call(4, "degree", "count", 5.0, [(3, 32, 10, 5.0)])]
+    n, nnz = 1000, 8000
+    f = bench.frontend_roofline(calls, 1, n, nnz)
+    C = 8 * (n + 1) + 4 * nnz
+    assert f["k=4 degree count"]["pre_list"]["bytes"] == C + n
+    assert f["k=4 color count"]["orientation"]["bytes"] == 3 * (C + 5 * n) + 4 * (n + 1) + 2 * nnz
+    o = f["k=4 degree count"]["orientation"]
+    assert abs(o["frac"] - o["bytes"] / 2e-3 / 1e9 / f["peak_GB_s"]) < 1e-12
+
+
+def test_golden_check_raises_on_mismatch():
+    gold = {"k=4 color": {"count": 10, "checksum": 77}, "k=5 color": {"count": 3}}
+    ok = [(4, "color", "count", 10, None), (4, "color", "list", 10, 77), (5, "color", "count", 3, None)]
+    assert bench.check_golden(ok, gold) == ["k=4 color count count", "k=4 color list checksum",
+                                            "k=4 color list count", "k=5 color count count"]
+    with pytest.raises(AssertionError):
+        bench.check_golden([(4, "color", "list", 10, 78)], gold)
+    with pytest.raises(AssertionError):
+        bench.check_golden([(5, "color", "count", 4, None)], gold)
 
 
 def _free_port():

@@ -317,6 +317,9 @@ def test_rmat20_full_size_counts(kcl, rmat20, k):
         key = "k=%d %s" % (k, o)
         if key in gold:
             assert counts[o] == gold[key]["count"], key
+        if key in gold and "checksum" in gold[key]:  # the oracle's full listing checksum
+            c, s, _, _ = kcl.kcl_list(g, k, o, None)
+            assert (c, s) == (gold[key]["count"], gold[key]["checksum"]), key
     # per-root parity on a seeded sample: the heaviest roots plus random ones
     for o in ORDS:
         pr = torch.zeros(n, dtype=torch.int64, device="cuda")

@@ -131,3 +131,5 @@ def test_example4_merge_work(fig1):
     assert r["counters"]["merge_elems"] == 12 + 4 + 3 + 5
     assert r["counters"]["intersections"] == 5
     assert r["counters"]["roots"] == 2 and r["counters"]["max_outdeg"] == 4
+    # every root has d+ <= 32: one bitmap word per merge join
+    assert r["counters"]["bitrow_words"] == 5

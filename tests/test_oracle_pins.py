@@ -352,3 +352,21 @@ def test_validate_matches_the_definition_on_every_tiny_input():
         rp = np.cumsum([0] + [len(r) for r in rows]).astype(np.uint64)
         col = np.array([v for r in rows for v in r], np.uint32)
         assert oracle.validate(rp, col) == _valid_by_definition(n, rp, col)
+
+
+@pytest.mark.parametrize("n", [40, 70])
+def test_sdegree_bitrow_words_closed_form_on_Kn(n):
+    """SDegree's bitmap-width work counter on K_n (k = 3, no preprocessing),
+    derived by hand.  All degrees are equal, so the degree DAG is by id: root
+    u has d+ = n-1-u out-neighbours v > u and is a root when d+ >= 2 (u <=
+    n-3).  Its call is at level 2, where a candidate v is merged unless
+    d+_v <= 0 (v = n-1): n-2-u joins, (n-2)(n-1)/2 in all.  Each join at root
+    u counts ceil((n-1-u) / 32) words."""
+    rp, col = complete(n)
+    r = oracle.sdegree(rp, col, 3, preprocess=False, count_only=True)
+    joins = sum(n - 2 - u for u in range(n - 2))
+    assert joins == (n - 2) * (n - 1) // 2
+    words = sum((n - 2 - u) * -(-(n - 1 - u) // 32) for u in range(n - 2))
+    assert r["count"] == comb(n, 3)
+    assert r["counters"]["intersections"] == joins
+    assert r["counters"]["bitrow_words"] == words
