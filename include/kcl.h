@@ -285,6 +285,12 @@ kcl_status kcl_scratch_bytes(const kcl_graph *g, uint64_t *workspace, uint64_t *
  *   children (the EdgeParallel units of Section IX-C) after the shared build;
  *   0 = all of them (default), 1 = one warp walks the whole subtree
  *   (NodeParallel), k = at most k warps.
+ * sdegree_split[c], bitcol_split[c]: work splitting of heavy roots across
+ *   CTAs in the CTA-per-root classes (split depth 1: a root's first-level
+ *   children, the edges <u, v> of Section IX-C, are the units).  A CTA that
+ *   runs out of roots rebuilds the subproblem of a root still in progress on
+ *   another CTA and takes over some of its children when at least t =
+ *   split[c] of them are left; 0 = off (default).
  * A graph starts with the defaults; views and batches start with the
  * defaults too. */
 typedef struct {
@@ -293,6 +299,8 @@ typedef struct {
     uint32_t sdegree_bitmap[KCL_MAX_CLASSES];
     uint32_t sdegree_cta_warps[KCL_MAX_CLASSES];
     uint32_t bitcol_cta_warps[KCL_MAX_CLASSES];
+    uint32_t sdegree_split[KCL_MAX_CLASSES];
+    uint32_t bitcol_split[KCL_MAX_CLASSES];
 } kcl_tuning;
 kcl_status kcl_get_tuning(const kcl_graph *g, kcl_tuning *t);
 kcl_status kcl_set_tuning(kcl_graph *g, const kcl_tuning *t);
@@ -302,7 +310,8 @@ kcl_status kcl_set_tuning(kcl_graph *g, const kcl_tuning *t);
  * later candidate must be 2% faster).  For KCL_ORDER_DEGREE it tunes
  * sdegree_bitmap first (candidates 0, 4, 64, 0xFFFFFFFF), then that mode's
  * galloping array (0, 40, 80, 160, 400); for both orderings it then tunes
- * that path's cta_warps array (0, 4, 8).  The tuning
+ * that path's cta_warps array (0, 4, 8) and its split array (0, 2, 8, 32).
+ * The tuning
  * is stored in g and copied to *out when out is not NULL.  Timing stays as
  * the caller left it.  Errors: those of kcl_count / kcl_list. */
 kcl_status kcl_autotune(kcl_graph *g, uint32_t k, kcl_ordering ord, int listing, kcl_tuning *out);

@@ -66,7 +66,9 @@ class _Tuning(ctypes.Structure):
                 ("sdegree_gallop_list", ctypes.c_uint32 * KCL_MAX_CLASSES),
                 ("sdegree_bitmap", ctypes.c_uint32 * KCL_MAX_CLASSES),
                 ("sdegree_cta_warps", ctypes.c_uint32 * KCL_MAX_CLASSES),
-                ("bitcol_cta_warps", ctypes.c_uint32 * KCL_MAX_CLASSES)]
+                ("bitcol_cta_warps", ctypes.c_uint32 * KCL_MAX_CLASSES),
+                ("sdegree_split", ctypes.c_uint32 * KCL_MAX_CLASSES),
+                ("bitcol_split", ctypes.c_uint32 * KCL_MAX_CLASSES)]
 
     def as_dict(self):
         return {f: [int(x) for x in getattr(self, f)] for f, _ in self._fields_}

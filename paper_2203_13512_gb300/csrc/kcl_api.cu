@@ -61,7 +61,7 @@ void free_workspace(Workspace &w) {
     void *ptrs[] = {w.alive, w.alive_core, w.cdeg, w.key, w.peel_deg, w.frontier_a, w.frontier_b,
                     w.parent, w.comp_n, w.comp_sdeg, w.comp_flag, w.outdeg, w.optr, w.oadj,
                     w.roots, w.hist, w.scan_tmp, w.queue, w.members, w.comp_slot, w.arena, w.res,
-                    w.peel};
+                    w.peel, w.slots};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (w.h_res) cudaFreeHost(w.h_res);
@@ -110,6 +110,7 @@ kcl_status ensure_workspace(kcl_graph *g) {
     KCL_TRY(dev_alloc(&w.comp_slot, n));
     KCL_TRY(dev_alloc(&w.res, 1));
     KCL_TRY(dev_alloc(&w.peel, 1));
+    KCL_TRY(dev_alloc(&w.slots, kMaxSplitSlots));
     if (cudaMallocHost((void **)&w.h_res, sizeof(DevResult)) != cudaSuccess) {
         (void)cudaGetLastError();
         w.h_res = nullptr;
@@ -821,7 +822,7 @@ kcl_status kcl_scratch_bytes(const kcl_graph *g, uint64_t *workspace, uint64_t *
              + 4 * 2                                // outdeg, optr extra entry
              + 4 * half                             // oadj
              + 4 * (3 * n + 1024) + 4 * (n / 1024 + 1024) + 4 * 64
-             + sizeof(DevResult) + sizeof(PeelCtl);
+             + sizeof(DevResult) + sizeof(PeelCtl) + 8 * kMaxSplitSlots;
     }
     *workspace = ws;
     *arena = (uint64_t)w.arena_words * 4;
@@ -895,6 +896,11 @@ kcl_status kcl_autotune(kcl_graph *g, uint32_t k, kcl_ordering ord, int listing,
         st = tune_knob(g, k, ord, listing,
                        ord == KCL_ORDER_DEGREE ? g->tuning.sdegree_cta_warps : g->tuning.bitcol_cta_warps,
                        warps_cand, 3);
+    static const uint32_t split_cand[] = {0, 2, 8, 32};
+    if (st == KCL_OK)
+        st = tune_knob(g, k, ord, listing,
+                       ord == KCL_ORDER_DEGREE ? g->tuning.sdegree_split : g->tuning.bitcol_split,
+                       split_cand, 4);
     if (!was_enabled) kcl_enable_timing(g, 0);
     if (st != KCL_OK) return st;
     if (out) *out = g->tuning;

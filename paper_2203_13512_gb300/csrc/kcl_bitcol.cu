@@ -218,18 +218,40 @@ __device__ void build_sub(uint32_t d, uint32_t base, uint32_t Wrt, const uint32_
             G::sync();
         }
 
-    // greedy colouring (one warp); colour class c is kept as row c-1 of B
+    // greedy colouring (one warp); colour class c is kept as row c-1 of B.
+    // Vertex v's row of A is staged once in a 16-byte-aligned scratch (the
+    // first-level child list, unused until the DFS), the next vertex's row
+    // is fetched while v is tested, and lane i tests colour c0 + i + 1 with
+    // 128-bit reads of the class row and broadcast reads of v's row.
     if (warp == 0) {
         uint32_t ncol = 0;
+        uint32_t *arow = reinterpret_cast<uint32_t *>(
+            (reinterpret_cast<uintptr_t>(s.pend) + 15) & ~static_cast<uintptr_t>(15));
+        const bool vec = (W & 3u) == 0 && (WPB & 3u) == 0;
+        uint32_t pf = lane < W ? s.A[(s.pre[0] & 0xFFFFu) * WP + lane] : 0u;  // next row, first 32 words
         for (uint32_t t = 0; t < d; t++) {
-            uint32_t v = s.pre[t] & 0xFFFFu;
+            const uint32_t v = s.pre[t] & 0xFFFFu;
+            if (lane < W) arow[lane] = pf;
+            for (uint32_t w = lane + 32; w < W; w += 32) arow[w] = s.A[v * WP + w];
+            __syncwarp();
+            if (t + 1 < d) pf = lane < W ? s.A[(s.pre[t + 1] & 0xFFFFu) * WP + lane] : 0u;
             uint32_t chosen = 0;
             for (uint32_t c0 = 0;; c0 += 32) {
                 uint32_t c = c0 + lane + 1;
                 bool fits = false;
                 if (c <= ncol) {
                     uint32_t acc = 0;
-                    for (uint32_t w = 0; w < W; w++) acc |= s.A[v * WP + w] & s.B[(c - 1) * WPB + w];
+                    const uint32_t *cls = s.B + (c - 1) * WPB;
+                    if (vec) {
+                        const uint4 *a4 = reinterpret_cast<const uint4 *>(arow);
+                        const uint4 *b4 = reinterpret_cast<const uint4 *>(cls);
+                        for (uint32_t w = 0; w < (W >> 2) && !acc; w++) {
+                            const uint4 a = a4[w], b = b4[w];
+                            acc = (a.x & b.x) | (a.y & b.y) | (a.z & b.z) | (a.w & b.w);
+                        }
+                    } else {
+                        for (uint32_t w = 0; w < W; w++) acc |= arow[w] & cls[w];
+                    }
                     fits = acc == 0;
                 } else if (c == ncol + 1) {
                     fits = true;
@@ -304,6 +326,8 @@ struct Emit {
     const uint32_t *idmap;         // listing: vertex -> output id, or null (identity)
     uint32_t prune;                // 1: Lemma 1 colour prune (0 only for ablations)
     uint32_t dfs_warps;            // CTA form: warps walking the children (0 = all)
+    unsigned long long *slots;     // CTA form: work-splitting slots (one per CTA)
+    uint32_t split;                // CTA form: help a root with >= split children left (0 = off)
 };
 
 struct View {  // read-only view of a built subproblem, per warp
@@ -771,8 +795,9 @@ __global__ void __launch_bounds__(128, 8) k_bitcol_warp(uint32_t k, const uint32
 // CTA per root: the subproblem is built once by the whole CTA (A and/or B in
 // a global arena slice when they do not fit), then the root's first-level
 // children are handed out to the warps, heaviest first.
+// At least 1024 threads per SM (two 512-thread CTAs): at most 64 registers.
 template <int NW, bool LIST, bool AG, bool BG>
-__global__ void __launch_bounds__(NW * 32) k_bitcol_cta(uint32_t k, uint32_t W, uint32_t D,
+__global__ void __launch_bounds__(NW * 32, (32 / NW > 0 ? 32 / NW : 1)) k_bitcol_cta(uint32_t k, uint32_t W, uint32_t D,
                                                        const uint32_t *__restrict__ optr,
                                                        const uint32_t *__restrict__ oadj,
                                                        const uint32_t *__restrict__ roots,
@@ -793,13 +818,32 @@ __global__ void __launch_bounds__(NW * 32) k_bitcol_cta(uint32_t k, uint32_t W, 
     uint32_t *Bg = BG ? slice + (AG ? rows_a : 0) : nullptr;
     const Sub s = sub_ptrs(smem, L, Ag, Bg);
     uint32_t *stack = smem + L.total + warp * dfs_words(W, k);
+    __shared__ int help_slot;  // -1: own root from the queue; else the slot of the root helped
     unsigned long long cnt = 0, cks = 0;
+    bool queue_done = false;
     for (;;) {
-        if (threadIdx.x == 0) root_idx = atomicAdd(queue, 1u);
+        if (threadIdx.x == 0) {
+            root_idx = queue_done ? end - begin : atomicAdd(queue, 1u);
+            help_slot = -1;
+        }
         __syncthreads();
-        const uint32_t idx = root_idx;
-        __syncthreads();
-        if (idx >= end - begin) break;
+        uint32_t idx = root_idx;
+        int helping = -1;
+        __syncthreads();  // every thread has read root_idx before it is rewritten
+        if (idx >= end - begin) {
+            queue_done = true;
+            // no root left: help the root with the most children left
+            if (!em.split || k == 3) break;
+            if (warp == 0) {
+                uint32_t pos = 0;
+                const int j = split_pick(em.slots, gridDim.x, blockIdx.x, em.split, &pos);
+                if (lane == 0) { help_slot = j; root_idx = pos; }
+            }
+            __syncthreads();
+            helping = help_slot;
+            idx = root_idx;
+            if (helping < 0 || idx >= end - begin) break;
+        }
         const uint32_t u = roots[begin + idx];
         const uint32_t base = optr[u], d = optr[u + 1] - base;
         const unsigned long long before = cnt;
@@ -820,9 +864,15 @@ __global__ void __launch_bounds__(NW * 32) k_bitcol_cta(uint32_t k, uint32_t W, 
             if (warp < nd) leaf<LIST>(v, stack, dw, 0, warp, nd, path, sortedR, em, res, cnt, cks);
         } else {
             const uint32_t nch = root_children<NW>(v, s);
+            // children are taken from this CTA's slot (own root) or the
+            // helped CTA's slot when splitting is on, else from shared memory
+            if (em.split && helping < 0 && threadIdx.x == 0) split_publish(em.slots + blockIdx.x, idx, nch);
+            __syncthreads();
             for (; warp < nd;) {
                 uint32_t i = 0;
-                if (lane == 0) i = atomicAdd(&s.meta[2], 1u);
+                if (lane == 0)
+                    i = em.split ? split_claim(em.slots + (helping >= 0 ? (uint32_t)helping : blockIdx.x), idx)
+                                 : atomicAdd(&s.meta[2], 1u);
                 i = __shfl_sync(kFull, i, 0);
                 if (i >= nch) break;
                 dfs_child<LIST>(v, s.pend[i], stack, em, res, cnt, cks);
@@ -1010,7 +1060,7 @@ int launch_bitcol(const kcl_graph *g, uint32_t k, Workspace &w, const uint32_t *
                   int n_classes, const ListArgs &la, cudaStream_t s) {
     // class c covers root positions [class_begin[c], c ? class_begin[c-1] : n_roots)
     Emit em{la.ring, la.capacity, la.wrap, la.per_root_cks, la.idmap,
-            (g->options & KCL_OPT_NO_COLOR_PRUNE) ? 0u : 1u, 0u};
+            (g->options & KCL_OPT_NO_COLOR_PRUNE) ? 0u : 1u, 0u, w.slots, 0u};
     int launches = 0;
     cudaMemsetAsync(w.queue, 0, 64 * sizeof(unsigned), s);
     for (int c = 0; c < n_classes; c++) {
@@ -1020,6 +1070,11 @@ int launch_bitcol(const kcl_graph *g, uint32_t k, Workspace &w, const uint32_t *
         const ClassCfg &cc = kClass[c];
         unsigned *q = w.queue + c;
         em.dfs_warps = g->tuning.bitcol_cta_warps[c];
+        em.split = 0;
+        if (cc.cta && g->tuning.bitcol_split[c]) {
+            em.split = g->tuning.bitcol_split[c];
+            cudaMemsetAsync(w.slots, 0xFF, kMaxSplitSlots * sizeof(unsigned long long), s);
+        }
         uint32_t Wl = cc.W, Dl = 32 * cc.W;
         if (cc.cta) class_layout(c, la.max_outdeg, &Wl, &Dl);
         const size_t smem = cc.cta ? class_smem(c, k, Wl, Dl) : class_smem(c, k);
@@ -1044,7 +1099,9 @@ int launch_bitcol(const kcl_graph *g, uint32_t k, Workspace &w, const uint32_t *
         } else {
             uint32_t blocks = (cc.ag || cc.bg) ? (uint32_t)g->num_sms * arena_slices_per_sm(c)
                                                : (uint32_t)g->num_sms * 4;
-            if (blocks > end - begin) blocks = end - begin;
+            // without splitting, CTAs beyond the number of roots would idle
+            if (!em.split && blocks > end - begin) blocks = end - begin;
+            if (blocks > kMaxSplitSlots) blocks = kMaxSplitSlots;
             const int nw = class_warps(c, k, Wl, Dl);
 #define KCL_C(NWV, AGV, BGV)                                                                          \
     if (la.listing) launch_cta<NWV, true, AGV, BGV>(k, Wl, Dl, nw, w, begin, end, q, em, la.per_root, smem, blocks, g->num_sms, s); \

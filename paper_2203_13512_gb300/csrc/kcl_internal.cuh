@@ -79,6 +79,7 @@ struct Workspace {
     uint32_t *members = nullptr;     // n: clique-component members (listing)
     uint32_t *comp_slot = nullptr;   // n: clique-component slot (listing)
     uint32_t *arena = nullptr;       // global scratch for large subproblems
+    unsigned long long *slots = nullptr;  // work-splitting slots, one per CTA of a launch
     size_t arena_words = 0;
     DevResult *res = nullptr;
     DevResult *h_res = nullptr;      // pinned host mirror
@@ -183,6 +184,63 @@ __device__ __forceinline__ uint32_t *ring_rec(uint32_t *ring, unsigned long long
         return nullptr;
     }
     return ring + s * k;
+}
+
+// ---------------------------------------------------------- work splitting
+// Heavy roots are shared between CTAs (the EdgeParallel units of Section
+// IX-C: a root's first-level children, the edges <u, v>).  Every CTA of a
+// CTA-per-root launch publishes the root it works on in its slot, one 64-bit
+// word: (root position << 32) | (first-level children << 16) | next child.
+// The CTA's warps take children by advancing `next`; a CTA that finds the
+// root queue empty picks the slot with the most children left, rebuilds that
+// root's subproblem (the build is deterministic, so the child list is the
+// same) and takes children from the same slot.  Claims are single
+// compare-and-swaps that fail once the slot holds another root, so no
+// child is taken twice or lost, and nothing waits on another CTA.
+constexpr unsigned long long kSlotIdle = ~0ull;
+constexpr uint32_t kNoChild = 0xFFFFFFFFu;
+
+__device__ __forceinline__ void split_publish(unsigned long long *slot, uint32_t pos, uint32_t nch) {
+    atomicExch(slot, ((unsigned long long)pos << 32) | ((unsigned long long)nch << 16));
+}
+
+// Next child (its position in the child list) of root position `pos`
+// published in `slot`, or kNoChild when none is left or the slot moved on.
+__device__ __forceinline__ uint32_t split_claim(unsigned long long *slot, uint32_t pos) {
+    unsigned long long old = *reinterpret_cast<volatile unsigned long long *>(slot);
+    for (uint32_t tries = 0; tries < (1u << 20); tries++) {  // bounded retries under contention
+        if ((uint32_t)(old >> 32) != pos) return kNoChild;
+        const uint32_t nch = (uint32_t)(old >> 16) & 0xFFFFu, next = (uint32_t)old & 0xFFFFu;
+        if (next >= nch) return kNoChild;
+        const unsigned long long got = atomicCAS(slot, old, old + 1);
+        if (got == old) return next;
+        old = got;
+    }
+    return kNoChild;
+}
+
+// Run by one warp: the slot (other than `me`) with the most children left,
+// at least min_left; -1 if none.  *pos receives its root position.
+__device__ __forceinline__ int split_pick(unsigned long long *slots, uint32_t nslots, uint32_t me,
+                                          uint32_t min_left, uint32_t *pos) {
+    const unsigned lane = threadIdx.x & 31u;
+    uint32_t best_left = 0, best = 0xFFFFFFFFu, best_pos = 0;
+    for (uint32_t j = lane; j < nslots; j += 32) {
+        const unsigned long long v = *reinterpret_cast<volatile unsigned long long *>(slots + j);
+        if (v == kSlotIdle || j == me) continue;
+        const uint32_t nch = (uint32_t)(v >> 16) & 0xFFFFu, next = (uint32_t)v & 0xFFFFu;
+        const uint32_t left = nch > next ? nch - next : 0u;
+        if (left >= min_left && left > best_left) { best_left = left; best = j; best_pos = (uint32_t)(v >> 32); }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const uint32_t l2 = __shfl_xor_sync(0xffffffffu, best_left, o);
+        const uint32_t b2 = __shfl_xor_sync(0xffffffffu, best, o);
+        const uint32_t p2 = __shfl_xor_sync(0xffffffffu, best_pos, o);
+        if (l2 > best_left || (l2 == best_left && b2 < best)) { best_left = l2; best = b2; best_pos = p2; }
+    }
+    *pos = best_pos;
+    return best_left ? (int)best : -1;
 }
 
 // Inclusive prefix sum over the 32 lanes of a warp (all lanes active).
@@ -338,6 +396,8 @@ struct ListArgs {
     cudaEvent_t *class_ev = nullptr;             // timing: 2 events per class, or null
     uint32_t max_outdeg = 0;                     // largest root out-degree of the call
 };
+// Slots for the work splitting of one launch (at most this many CTAs).
+constexpr uint32_t kMaxSplitSlots = 4096;
 // Records class_ev[2c] / [2c+1] (when timing) around the launch of class c.
 inline void class_mark(const ListArgs &la, int c, int end, cudaStream_t s) {
     if (la.class_ev) cudaEventRecord(la.class_ev[2 * c + end], s);

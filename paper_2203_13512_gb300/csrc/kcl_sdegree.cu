@@ -41,6 +41,8 @@ struct Emit {
     int wrap;
     unsigned long long *root_cks;  // listing: per-root checksum sums, or null
     const uint32_t *idmap;         // listing: vertex -> output id, or null (identity)
+    unsigned long long *slots;     // CTA form: work-splitting slots (one per CTA)
+    uint32_t split;                // CTA form: help a root with >= split children left (0 = off)
 };
 
 // lower_bound of x in a sorted list
@@ -1069,11 +1071,33 @@ __global__ void __launch_bounds__(512) k_sdegree_cta(uint32_t k, uint32_t D, con
     uint32_t *bits = slice;
     uint16_t *ladj_g = reinterpret_cast<uint16_t *>(slice + (((size_t)D * L.WPD + 3) & ~(size_t)3));
     unsigned long long cnt = 0, cks = 0;
+    __shared__ int help_slot;  // -1: own root from the queue; else the slot of the root helped
+    unsigned long long *my_slot = em.slots + blockIdx.x;
+    bool queue_done = false;
     for (;;) {
-        if (tid == 0) meta[15] = atomicAdd(queue, 1u);
+        if (tid == 0) {
+            meta[15] = queue_done ? end - begin : atomicAdd(queue, 1u);
+            help_slot = -1;
+        }
         __syncthreads();
-        const uint32_t idx = meta[15];
-        if (idx >= end - begin) break;
+        uint32_t idx = meta[15];
+        int helping = -1;
+        __syncthreads();  // every thread has read meta[15] before it is rewritten
+        if (idx >= end - begin) {
+            queue_done = true;
+            // no root left: help the root with the most children left
+            if (!em.split || k == 3) break;
+            if (warp == 0) {
+                uint32_t pos = 0;
+                const int j = split_pick(em.slots, gridDim.x, blockIdx.x, em.split, &pos);
+                if (lane == 0) { help_slot = j; meta[15] = pos; }
+            }
+            __syncthreads();
+            helping = help_slot;
+            idx = meta[15];
+            if (helping < 0 || idx >= end - begin) break;
+        }
+        unsigned long long *slot = helping >= 0 ? em.slots + helping : my_slot;
         const uint32_t u = roots[begin + idx];
         const uint32_t base = optr[u], d = optr[u + 1] - base;
         const unsigned long long before = cnt;
@@ -1261,13 +1285,17 @@ __global__ void __launch_bounds__(512) k_sdegree_cta(uint32_t k, uint32_t D, con
             for (uint32_t i = tid; i < round4(d); i += nth) p0[i] = i < d ? (uint16_t)i : kPad;
         }
         __syncthreads();
+        if (em.split && k > 3) {  // share the children with CTAs that run out of roots
+            if (helping < 0 && tid == 0) split_publish(my_slot, idx, meta[8]);
+            __syncthreads();
+        }
         if (bitrows && warp < nw_dfs) {
             const BView bv{smem + L.total, rs, d, meta[10], meta[11], v.u, k};
             uint32_t *stack = smem + L.total + meta[7] + warp * sw;
             const uint32_t n0 = meta[8];
             for (;;) {
                 uint32_t i = 0;
-                if (lane == 0) i = atomicAdd(&meta[9], 1u);
+                if (lane == 0) i = em.split ? split_claim(slot, idx) : atomicAdd(&meta[9], 1u);
                 i = __shfl_sync(kFull, i, 0);
                 if (i >= n0) break;
                 bdfs_child<LIST>(bv, p0[i], stack, em, res, cnt, cks);
@@ -1289,7 +1317,7 @@ __global__ void __launch_bounds__(512) k_sdegree_cta(uint32_t k, uint32_t D, con
                 const uint32_t n0 = meta[8];
                 for (;;) {
                     uint32_t i = 0;
-                    if (lane == 0) i = atomicAdd(&meta[9], 1u);
+                    if (lane == 0) i = em.split ? split_claim(slot, idx) : atomicAdd(&meta[9], 1u);
                     i = __shfl_sync(kFull, i, 0);
                     if (i >= n0) break;
                     ldfs_child<LIST>(v, p0[i], st, em, res, cnt, cks);
@@ -1423,7 +1451,9 @@ void launch_cta(uint32_t k, uint32_t D, Workspace &w, uint32_t begin, uint32_t e
     if (occ < 1) occ = 1;
     if (occ > (int)cta_slices_per_sm(D)) occ = (int)cta_slices_per_sm(D);  // arena slices per SM
     uint32_t blocks = (uint32_t)num_sms * occ;
-    if (blocks > end - begin) blocks = end - begin;
+    // without splitting, CTAs beyond the number of roots would idle
+    if (!em.split && blocks > end - begin) blocks = end - begin;
+    if (blocks > kMaxSplitSlots) blocks = kMaxSplitSlots;
     kern<<<blocks, threads, smem, s>>>(k, D, w.optr, w.oadj, w.key, w.roots, begin, end, queue,
                                        w.arena, (uint32_t)(smem / 4), em, gallop, bitmap, dfs_warps,
                                        per_root, w.res);
@@ -1464,7 +1494,7 @@ size_t sdegree_arena_words(uint32_t k, int num_sms, uint32_t max_outdeg) {
 
 int launch_sdegree(const kcl_graph *g, uint32_t k, Workspace &w, const uint32_t *class_begin,
                    int n_classes, const ListArgs &la, cudaStream_t s) {
-    Emit em{la.ring, la.capacity, la.wrap, la.per_root_cks, la.idmap};
+    Emit em{la.ring, la.capacity, la.wrap, la.per_root_cks, la.idmap, w.slots, 0u};
     int launches = 0;
     cudaMemsetAsync(w.queue, 0, 64 * sizeof(unsigned), s);
     for (int c = 0; c < n_classes; c++) {
@@ -1480,6 +1510,9 @@ int launch_sdegree(const kcl_graph *g, uint32_t k, Workspace &w, const uint32_t 
         const uint32_t bm = g->tuning.sdegree_bitmap[c];
         const uint32_t dw = g->tuning.sdegree_cta_warps[c];
         const int ns = g->num_sms;
+        const bool cta_form = c < kCtaClasses && (c >= kWarpClasses || la.listing);
+        em.split = cta_form ? g->tuning.sdegree_split[c] : 0u;
+        if (em.split) cudaMemsetAsync(w.slots, 0xFF, kMaxSplitSlots * sizeof(unsigned long long), s);
         class_mark(la, c, 0, s);
         if (c < kWarpClasses) {
             // listing hashes every clique: a root's cost grows with its clique

@@ -367,10 +367,12 @@ def test_autotune_keeps_results(kcl, small_workload):
     assert all(v in (0, 40, 80, 160, 400) for v in t["sdegree_gallop"] + t["sdegree_gallop_list"])
     assert all(v in (0, 4, 64, 0xFFFFFFFF) for v in t["sdegree_bitmap"])
     assert all(v in (0, 4, 8) for v in t["sdegree_cta_warps"] + t["bitcol_cta_warps"])
+    assert all(v in (0, 2, 8, 32) for v in t["sdegree_split"] + t["bitcol_split"])
     assert kcl.kcl_count(g, 5, "degree") == oracle.plain(rp, col, 5)[0]
     assert kcl.kcl_list(g, 4, "degree", None)[:2] == oracle.plain(rp, col, 4)
     tc = kcl.kcl_autotune(g, 5, "color")
-    assert {f: tc[f] for f in tc if f != "bitcol_cta_warps"} == {f: t[f] for f in t if f != "bitcol_cta_warps"}
+    mine = ("bitcol_cta_warps", "bitcol_split")
+    assert {f: tc[f] for f in tc if f not in mine} == {f: t[f] for f in t if f not in mine}
     assert kcl.kcl_count(g, 5, "color") == oracle.plain(rp, col, 5)[0]
 
 
@@ -521,3 +523,69 @@ def test_colouring_matches_oracle_on_sampled_roots(kcl, scale, k):
         assert list(got_nb) == nb, u
         _, want = oracle.colour_graph(grp, gcol)
         assert np.array_equal(got_co, want), u
+
+
+def test_rmat20_k6_sampled_roots(kcl, rmat20):
+    """k = 6 on the full-size R-MAT scale 20 graph (2.8e13 cliques, beyond
+    the oracle): the two orderings agree on the count, and the per-root
+    counts of the seeded sample stored by tests/golden/make_rmat20_work.py
+    (the 3 heaviest roots, 40 at random, 2 per out-degree bucket) equal the
+    oracle's."""
+    import torch
+    gold = _golden_rmat20()
+    rp, col = rmat20
+    n = len(rp) - 1
+    g = kcl.kcl_load_csr(rp, col)
+    totals = {}
+    for o in ORDS:
+        e = gold.get("k=6 %s" % o, {}).get("sample")
+        assert e, "golden sample missing for k=6 %s" % o
+        pr = torch.zeros(n, dtype=torch.int64, device="cuda")
+        tot, pre = kcl.kcl_count_per_root(g, 6, o, pr)
+        per = pr.cpu().numpy().astype(np.uint64)
+        assert int(per.sum()) + pre == tot
+        roots = np.array(e["roots"], np.int64)
+        assert [int(x) for x in per[roots]] == e["per_root"], o
+        od = kcl.kcl_stage_info(g, 6, o)["outdeg"]
+        assert [int(x) for x in od[roots]] == e["outdeg"], o
+        totals[o] = tot
+    assert totals["degree"] == totals["color"]
+
+
+@pytest.mark.parametrize("split", [1, 3])
+def test_work_splitting_keeps_results(kcl, split):
+    """Heavy roots shared between CTAs (a CTA that runs out of roots rebuilds
+    a root still in progress and takes over first-level children while at
+    least `split` are left): counts, checksums, listings and per-root counts
+    are those of the oracle, in both orderings."""
+    import torch
+    tune = {"sdegree_split": [split] * kcl.KCL_MAX_CLASSES,
+            "bitcol_split": [split] * kcl.KCL_MAX_CLASSES}
+    graphs = [kclgen.chung_lu(3000, 12000, 2.3, groups=3, group_size=(sz, sz), group_p=p, seed=sz)
+              for sz, p in ((170, 0.6), (260, 0.45))]
+    graphs.append(_near_complete(300))
+    for rp, col in graphs:
+        g = kcl.kcl_load_csr(rp, col)
+        kcl.kcl_set_tuning(g, tune)
+        n = len(rp) - 1
+        for k in (4, 5):
+            ref = oracle.plain(rp, col, k)
+            for o in ORDS:
+                assert kcl.kcl_count(g, k, o) == ref[0], (k, o)
+                assert kcl.kcl_list(g, k, o, None)[:2] == ref, (k, o)
+                pr = torch.zeros(n, dtype=torch.int64, device="cuda")
+                kcl.kcl_count_per_root(g, k, o, pr)
+                want = _oracle_mode(o)(rp, col, k, per_root=True, count_only=True)["per_root"]
+                assert np.array_equal(pr.cpu().numpy().astype(np.uint64), want), (k, o)
+    # the listed records themselves (4.7e6 4-cliques, compared as sorted rows)
+    rp, col = graphs[0]
+    g = kcl.kcl_load_csr(rp, col)
+    kcl.kcl_set_tuning(g, tune)
+    ref_c, ref_s, ref_l = oracle.plain(rp, col, 4, list_cap=5_000_000)
+    want = ref_l[np.lexsort(ref_l.T[::-1])]
+    for o in ORDS:
+        ring = _ring(kcl, 4, ref_c + 3)
+        c, s, w, trunc = kcl.kcl_list(g, 4, o, ring)
+        assert (c, s, w, trunc) == (ref_c, ref_s, ref_c, False)
+        got = ring[: w * 4].cpu().numpy().astype(np.uint32).reshape(-1, 4)
+        assert np.array_equal(got[np.lexsort(got.T[::-1])], want), o
