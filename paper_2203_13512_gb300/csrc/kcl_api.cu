@@ -227,11 +227,13 @@ bool run_peel_coop(kcl_graph *g, StageTimer &T) {
     Workspace &w = g->ws;
     cudaStream_t s = g->stream;
     if (cudaMemsetAsync(w.peel, 0, sizeof(PeelCtl), s) != cudaSuccess ||
-        cudaMemsetAsync(&w.peel->minv, 0xFF, sizeof(unsigned), s) != cudaSuccess) {
+        cudaMemsetAsync(w.peel->minv, 0xFF, sizeof(w.peel->minv), s) != cudaSuccess) {
         (void)cudaGetLastError();
         return false;
     }
-    int l = launch_peel_coop(g, w, w.peel, s);
+    // the remaining-vertex lists use the root-histogram scratch (3n + 1024
+    // words), which is free until the roots are sorted after the peel
+    int l = launch_peel_coop(g, w, w.peel, w.hist, w.hist + g->n, s);
     if (l < 0) {
         (void)cudaGetLastError();
         return false;

@@ -38,12 +38,16 @@ struct DevResult {
     unsigned int pad;
 };
 
-// Control block of the single-launch degeneracy peel (grid barrier state,
-// round counters, frontier sizes).
+// Control block of the single-launch degeneracy peel: grid barrier state,
+// the number of vertices to peel, frontier sizes (rotating over three rounds),
+// remaining-list sizes and minimum degrees (alternating over threshold
+// levels).  All zero at launch except minv, all ones.
 struct PeelCtl {
-    unsigned bar_count, bar_gen, error;
-    unsigned nin, nnext, minv, t, round, remaining, parity;
-    unsigned pad[6];
+    unsigned bar_count, bar_gen, error, remaining;
+    unsigned fcnt[3];
+    unsigned rcnt[2];
+    unsigned minv[2];
+    unsigned pad[3];
 };
 
 // One graph of a batch: its device CSR and its place in the disjoint union.
@@ -371,7 +375,10 @@ int launch_peel_update(const kcl_graph *g, Workspace &w, const uint32_t *fin, ui
                        uint32_t t, uint32_t round, uint32_t *fout, cudaStream_t s);
 int launch_peel_min(const kcl_graph *g, Workspace &w, cudaStream_t s);
 // Whole degeneracy peel in one cooperative launch; -1 if it cannot launch.
-int launch_peel_coop(const kcl_graph *g, Workspace &w, PeelCtl *ctl, cudaStream_t s);
+// rl0/rl1: two n-entry arrays for the compacted remaining-vertex lists (or
+// both null: every threshold rise scans all n vertices).
+int launch_peel_coop(const kcl_graph *g, Workspace &w, PeelCtl *ctl, uint32_t *rl0, uint32_t *rl1,
+                     cudaStream_t s);
 int launch_orient(const kcl_graph *g, uint32_t k, Workspace &w, cudaStream_t s);
 int launch_roots(const kcl_graph *g, uint32_t k, Workspace &w, uint32_t max_outdeg,
                  uint32_t *class_begin, const uint32_t *class_limits, int n_classes,

@@ -361,10 +361,21 @@ __global__ void k_peel_update(const uint64_t *__restrict__ rp, const uint32_t *_
 
 // The same peel in one cooperative launch (every block resident): rounds are
 // separated by a grid barrier instead of a kernel boundary and a host round
-// trip.  Control words live in PeelCtl; arrays written during the launch are
-// read with ld.global.cg (L2) so no stale L1 line is used.  Every barrier
-// wait is bounded: past kSpinLimit polls the block records an error, all
-// blocks leave, and the host reports KCL_ETIMEOUT.
+// trip.  Every block follows the same control flow, derived from counters
+// read after a barrier:
+//   a round with a non-empty frontier (a cascade) processes it and ends with
+//     one barrier; frontier counters rotate over three rounds (round r reads
+//     fcnt[r % 3], appends to fcnt[(r+1) % 3] and clears fcnt[(r+2) % 3],
+//     which every block read two barriers earlier);
+//   a round with an empty frontier raises t: a pass over the remaining
+//     vertices finds their minimum degree (barrier), a second pass selects
+//     those at or below t into the frontier and, when rl0/rl1 are given,
+//     compacts the vertices still remaining into the other list (barrier),
+//     so later passes touch only what is left.
+// Arrays written during the launch are read with ld.global.cg (L2) so no
+// stale L1 line is used.  Every barrier wait is bounded: past kSpinLimit
+// polls the block records an error, all blocks leave, and the host reports
+// KCL_ETIMEOUT.
 constexpr unsigned long long kSpinLimit = 1ull << 25;
 
 __device__ bool grid_barrier(PeelCtl *c, unsigned nblocks) {
@@ -386,7 +397,7 @@ __device__ bool grid_barrier(PeelCtl *c, unsigned nblocks) {
             while (*gen == g) {
                 if (*err) { ok = 0; break; }
                 if (++spins > kSpinLimit) { atomicExch(&c->error, 1u); ok = 0; break; }
-                __nanosleep(64);
+                __nanosleep(32);
             }
         }
         __threadfence();
@@ -396,85 +407,121 @@ __device__ bool grid_barrier(PeelCtl *c, unsigned nblocks) {
     return ok_s != 0;
 }
 
-__global__ void __launch_bounds__(512) k_peel_coop(uint32_t n, const uint64_t *__restrict__ rp,
-                                                   const uint32_t *__restrict__ col,
-                                                   const uint8_t *__restrict__ alive,
-                                                   const uint32_t *__restrict__ cdeg, uint32_t *pdeg,
-                                                   uint32_t *key, uint32_t *fa, uint32_t *fb,
-                                                   PeelCtl *c) {
+__global__ void __launch_bounds__(1024) k_peel_coop(uint32_t n, const uint64_t *__restrict__ rp,
+                                                    const uint32_t *__restrict__ col,
+                                                    const uint8_t *__restrict__ alive,
+                                                    const uint32_t *__restrict__ cdeg, uint32_t *pdeg,
+                                                    uint32_t *key, uint32_t *fa, uint32_t *fb,
+                                                    uint32_t *rl0, uint32_t *rl1, PeelCtl *c) {
     const unsigned nblocks = gridDim.x;
     const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
     const uint32_t nth = gridDim.x * blockDim.x;
     const unsigned lane = lane_id();
     volatile PeelCtl *vc = c;
+    const bool lists = rl0 != nullptr;
     {
         uint32_t cnt = 0;
-        for (uint32_t v = tid; v < n; v += nth) {
-            pdeg[v] = cdeg[v];
-            key[v] = 0xFFFFFFFFu;
-            cnt += alive[v] ? 1 : 0;
+        for (uint32_t v0 = tid - lane; v0 < n; v0 += nth) {  // warp-uniform trip count
+            const uint32_t v = v0 + lane;
+            bool a = false;
+            if (v < n) {
+                pdeg[v] = cdeg[v];
+                key[v] = 0xFFFFFFFFu;
+                a = alive[v] != 0;
+            }
+            cnt += a ? 1 : 0;
+            if (lists) {  // the first remaining list: every alive vertex
+                const unsigned m = __ballot_sync(0xffffffffu, a);
+                unsigned base = 0;
+                if (lane == 0 && m) base = atomicAdd(&c->rcnt[0], (unsigned)__popc(m));
+                base = __shfl_sync(0xffffffffu, base, 0);
+                if (a) rl0[base + __popc(m & ((1u << lane) - 1u))] = v;
+            }
         }
         cnt = __reduce_add_sync(0xffffffffu, cnt);
         if (lane == 0 && cnt) atomicAdd(&c->remaining, cnt);
     }
     if (!grid_barrier(c, nblocks)) return;
-    for (;;) {
-        const uint32_t remaining = vc->remaining;
-        if (remaining == 0) break;
-        uint32_t nin = vc->nin;
-        const uint32_t parity = vc->parity;
-        const uint32_t round = vc->round;
-        uint32_t t = vc->t;
-        uint32_t *fin = parity ? fb : fa;
-        uint32_t *fout = parity ? fa : fb;
+    uint32_t remaining = vc->remaining;
+    uint32_t round = 0, t = 0, level = 0;
+    while (remaining > 0) {
+        const uint32_t fi = round % 3u;
+        uint32_t *fin = (round & 1u) ? fb : fa;
+        uint32_t *fout = (round & 1u) ? fa : fb;
+        uint32_t nin = vc->fcnt[fi];
         if (nin == 0) {
-            // t rises to the minimum remaining degree; select every vertex at or below it
+            // t rises to the minimum remaining degree
+            const uint32_t lp = level & 1u;
+            const uint32_t *rl = lp ? rl1 : rl0;
+            uint32_t *rl_next = lp ? rl0 : rl1;
+            const uint32_t nr = lists ? vc->rcnt[lp] : n;
+            if (tid == 0 && lists) c->rcnt[lp ^ 1u] = 0;  // read at the previous level
             uint32_t mn = 0xFFFFFFFFu;
-            for (uint32_t v = tid; v < n; v += nth)
-                if (alive[v] && __ldcg(&key[v]) == 0xFFFFFFFFu) {
-                    uint32_t d = __ldcg(&pdeg[v]);
+            for (uint32_t i = tid; i < nr; i += nth) {
+                const uint32_t v = lists ? __ldcg(&rl[i]) : i;
+                if ((lists || alive[v]) && __ldcg(&key[v]) == 0xFFFFFFFFu) {
+                    const uint32_t d = __ldcg(&pdeg[v]);
                     mn = d < mn ? d : mn;
                 }
+            }
             mn = __reduce_min_sync(0xffffffffu, mn);
-            if (lane == 0 && mn != 0xFFFFFFFFu) atomicMin(&c->minv, mn);
+            if (lane == 0 && mn != 0xFFFFFFFFu) atomicMin(&c->minv[lp], mn);
             if (!grid_barrier(c, nblocks)) return;
-            const uint32_t mv = vc->minv;
+            const uint32_t mv = vc->minv[lp];
             if (mv > t) t = mv;
-            for (uint32_t v = tid; v < n; v += nth)
-                if (alive[v] && __ldcg(&key[v]) == 0xFFFFFFFFu && __ldcg(&pdeg[v]) <= t) {
-                    key[v] = round;
-                    fin[atomicAdd(&c->nin, 1u)] = v;
+            if (tid == 0) c->minv[lp ^ 1u] = 0xFFFFFFFFu;  // read at the previous level
+            // select the frontier; compact the rest into the other list
+            for (uint32_t i0 = tid - lane; i0 < nr; i0 += nth) {
+                const uint32_t i = i0 + lane;
+                bool sel = false, keep = false;
+                uint32_t v = 0;
+                if (i < nr) {
+                    v = lists ? __ldcg(&rl[i]) : i;
+                    if ((lists || alive[v]) && __ldcg(&key[v]) == 0xFFFFFFFFu) {
+                        sel = __ldcg(&pdeg[v]) <= t;
+                        keep = !sel;
+                    }
                 }
+                const unsigned ms = __ballot_sync(0xffffffffu, sel);
+                unsigned bs = 0;
+                if (lane == 0 && ms) bs = atomicAdd(&c->fcnt[fi], (unsigned)__popc(ms));
+                bs = __shfl_sync(0xffffffffu, bs, 0);
+                if (sel) {
+                    key[v] = round;
+                    fin[bs + __popc(ms & ((1u << lane) - 1u))] = v;
+                }
+                if (lists) {
+                    const unsigned mk = __ballot_sync(0xffffffffu, keep);
+                    unsigned bk = 0;
+                    if (lane == 0 && mk) bk = atomicAdd(&c->rcnt[lp ^ 1u], (unsigned)__popc(mk));
+                    bk = __shfl_sync(0xffffffffu, bk, 0);
+                    if (keep) rl_next[bk + __popc(mk & ((1u << lane) - 1u))] = v;
+                }
+            }
+            level++;
             if (!grid_barrier(c, nblocks)) return;
-            nin = vc->nin;
+            nin = vc->fcnt[fi];
             if (nin == 0) {  // cannot happen while vertices remain
                 if (tid == 0) atomicExch(&c->error, 2u);
                 return;
             }
         }
+        if (tid == 0) c->fcnt[(round + 2u) % 3u] = 0;  // every block read it two barriers ago
         // remove this round's vertices: lower the degrees of their remaining
         // neighbours; a neighbour reaching <= t joins the next round
+        uint32_t *fnext_cnt = &c->fcnt[(round + 1u) % 3u];
         for (uint32_t i = tid >> 5; i < nin; i += nth >> 5) {
-            uint32_t v = __ldcg(&fin[i]);
+            const uint32_t v = __ldcg(&fin[i]);
             for (uint64_t e = rp[v] + lane; e < rp[v + 1]; e += 32) {
-                uint32_t w = col[e];
+                const uint32_t w = col[e];
                 if (!alive[w] || __ldcg(&key[w]) != 0xFFFFFFFFu) continue;
-                uint32_t nd = atomicSub(&pdeg[w], 1u) - 1u;
+                const uint32_t nd = atomicSub(&pdeg[w], 1u) - 1u;
                 if (nd <= t && atomicCAS(&key[w], 0xFFFFFFFFu, round + 1) == 0xFFFFFFFFu)
-                    fout[atomicAdd(&c->nnext, 1u)] = w;
+                    fout[atomicAdd(fnext_cnt, 1u)] = w;
             }
         }
-        if (!grid_barrier(c, nblocks)) return;
-        if (tid == 0) {
-            c->remaining = remaining - (nin < remaining ? nin : remaining);
-            c->nin = c->nnext;
-            c->nnext = 0;
-            c->round = round + 1;
-            c->parity = parity ^ 1u;
-            c->t = t;
-            c->minv = 0xFFFFFFFFu;
-            __threadfence();
-        }
+        remaining -= nin < remaining ? nin : remaining;
+        round++;
         if (!grid_barrier(c, nblocks)) return;
     }
 }
@@ -793,17 +840,31 @@ int launch_peel_update(const kcl_graph *g, Workspace &w, const uint32_t *fin, ui
     return 1;
 }
 
-int launch_peel_coop(const kcl_graph *g, Workspace &w, PeelCtl *ctl, cudaStream_t s) {
-    static int blocks_per_sm = -1;
-    if (blocks_per_sm < 0) {
+constexpr int kPeelThreads = 1024;
+
+// Blocks of the cooperative peel for n vertices: one per SM (fewer arrivals
+// per grid barrier), none beyond what n needs; -1 if it cannot be resident.
+int peel_blocks(int num_sms, uint32_t n) {
+    static int per_sm = -1;
+    if (per_sm < 0) {
         int b = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_peel_coop, 512, 0) != cudaSuccess) b = 0;
-        blocks_per_sm = b > 2 ? 2 : b;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_peel_coop, kPeelThreads, 0) != cudaSuccess) {
+            (void)cudaGetLastError();
+            b = 0;
+        }
+        per_sm = b;
     }
-    if (blocks_per_sm <= 0) return -1;
-    int blocks = g->num_sms * blocks_per_sm;
-    uint64_t need = ((uint64_t)g->n + 511) / 512;
+    if (per_sm <= 0) return -1;
+    int blocks = num_sms;
+    const uint64_t need = ((uint64_t)n + kPeelThreads - 1) / kPeelThreads;
     if (need < (uint64_t)blocks) blocks = need ? (int)need : 1;
+    return blocks;
+}
+
+int launch_peel_coop(const kcl_graph *g, Workspace &w, PeelCtl *ctl, uint32_t *rl0, uint32_t *rl1,
+                     cudaStream_t s) {
+    int blocks = peel_blocks(g->num_sms, g->n);
+    if (blocks <= 0) return -1;
     uint32_t n = g->n;
     const uint64_t *rp = g->rp;
     const uint32_t *col = g->col;
@@ -811,8 +872,9 @@ int launch_peel_coop(const kcl_graph *g, Workspace &w, PeelCtl *ctl, cudaStream_
     const uint32_t *cdeg = w.cdeg;
     uint32_t *pdeg = w.peel_deg, *key = w.key, *fa = w.frontier_a, *fb = w.frontier_b;
     void *args[] = {&n, (void *)&rp, (void *)&col, (void *)&alive, (void *)&cdeg, &pdeg, &key, &fa,
-                    &fb, &ctl};
-    if (cudaLaunchCooperativeKernel((const void *)k_peel_coop, blocks, 512, args, 0, s) != cudaSuccess)
+                    &fb, &rl0, &rl1, &ctl};
+    if (cudaLaunchCooperativeKernel((const void *)k_peel_coop, blocks, kPeelThreads, args, 0, s) !=
+        cudaSuccess)
         return -1;
     return 1;
 }
@@ -881,15 +943,14 @@ kcl_status noalloc_setup(uint32_t **ptr, int *blocks) {
             (void)cudaGetLastError();
             return KCL_ECUDA;
         }
-        int sms = 0, per_sm = 0;
-        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kcl::k_peel_coop, 512, 0) !=
-                cudaSuccess ||
-            sms <= 0 || per_sm <= 0) {
+        int sms = 0;
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) {
             (void)cudaGetLastError();
             return KCL_ECUDA;
         }
-        noalloc_blocks[dev] = sms * (per_sm > 2 ? 2 : per_sm);
+        const int blocks = kcl::peel_blocks(sms, KCL_NOALLOC_MAX_VERTICES);
+        if (blocks <= 0) return KCL_ECUDA;
+        noalloc_blocks[dev] = blocks;
         noalloc_ptr[dev] = p;
     }
     *ptr = noalloc_ptr[dev];
@@ -909,7 +970,7 @@ extern "C" kcl_status kcl_degeneracy_order_noalloc(uint32_t n, const uint64_t *r
     int blocks = 0;
     kcl_status st = noalloc_setup(&S, &blocks);
     if (st != KCL_OK) return st;
-    uint64_t need = ((uint64_t)n + 511) / 512;
+    uint64_t need = ((uint64_t)n + kcl::kPeelThreads - 1) / kcl::kPeelThreads;
     if (need < (uint64_t)blocks) blocks = (int)need;
     cudaStream_t s = (cudaStream_t)stream;
     uint32_t *pdeg = S;
@@ -919,7 +980,7 @@ extern "C" kcl_status kcl_degeneracy_order_noalloc(uint32_t n, const uint64_t *r
     // the control block keeps the previous call's contents: clear it (minv
     // starts at all ones, everything else at zero)
     if (cudaMemsetAsync(ctl, 0, sizeof(kcl::PeelCtl), s) != cudaSuccess ||
-        cudaMemsetAsync(&ctl->minv, 0xFF, sizeof(unsigned), s) != cudaSuccess) {
+        cudaMemsetAsync(ctl->minv, 0xFF, sizeof(ctl->minv), s) != cudaSuccess) {
         (void)cudaGetLastError();
         return KCL_ECUDA;
     }
@@ -929,8 +990,10 @@ extern "C" kcl_status kcl_degeneracy_order_noalloc(uint32_t n, const uint64_t *r
     const uint8_t *al = alive;
     const uint32_t *deg = degree;
     uint32_t *key = round_out;
-    void *args[] = {&nn, (void *)&rp, (void *)&c, (void *)&al, (void *)&deg, &pdeg, &key, &fa, &fb, &ctl};
-    if (cudaLaunchCooperativeKernel((const void *)kcl::k_peel_coop, blocks, 512, args, 0, s) !=
+    uint32_t *rl0 = nullptr, *rl1 = nullptr;  // no room for remaining lists: full scans
+    void *args[] = {&nn, (void *)&rp, (void *)&c, (void *)&al, (void *)&deg, &pdeg, &key, &fa, &fb,
+                    &rl0, &rl1, &ctl};
+    if (cudaLaunchCooperativeKernel((const void *)kcl::k_peel_coop, blocks, kcl::kPeelThreads, args, 0, s) !=
         cudaSuccess) {
         (void)cudaGetLastError();
         return KCL_ECUDA;
