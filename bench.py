@@ -277,12 +277,55 @@ def run_ours(args, rank, world):
         "int_peaks": peaks,
         "stage_ms": stage_summary(per_call, args.steps),
     }
+    if not args.no_c1:
+        res["c1"] = run_c1(golden)
     if k6:
         tot = sum(v["count"] for v in k6.values())
         res["c2_k6"] = {"orderings": k6, "orderings_agree": len({v["count"] for v in k6.values()}) == 1,
                         "k_cliques_per_s": tot / (sum(v["ms"] for v in k6.values()) / 1e3)}
     g.free()
     return res
+
+
+def run_c1(golden, repeats=20):
+    """The small Chung-Lu workload (n = 10,000, 50,000 drawn pairs, exponent
+    2.5, 20 planted 12-cliques, seed 1), k = 5, degree ordering: kcl_count and
+    kcl_list (count + checksum) through the C ABI, median of `repeats` warm
+    calls (host wall clock, each call synchronous); `e2e` also copies the
+    graph in from host memory (validated on the device) and frees it.  The
+    count and checksum must equal the oracle's (tests/golden)."""
+    import kclgen
+    import paper_2203_13512_gb300 as kcl
+    rp, col = kclgen.chung_lu_planted_small(seed=1)
+    want = golden.get("c1 k=5")
+    g = kcl.kcl_load_csr(rp, col)
+    for _ in range(3):
+        kcl.kcl_count(g, 5, "degree")
+        kcl.kcl_list(g, 5, "degree", None)
+    tc, tl, te = [], [], []
+    for _ in range(repeats):
+        t = time.perf_counter()
+        c = kcl.kcl_count(g, 5, "degree")
+        tc.append(time.perf_counter() - t)
+        t = time.perf_counter()
+        c2, s, _, _ = kcl.kcl_list(g, 5, "degree", None)
+        tl.append(time.perf_counter() - t)
+        t = time.perf_counter()
+        g2 = kcl.kcl_load_csr(rp, col)
+        c3 = kcl.kcl_count(g2, 5, "degree")
+        c4, s2, _, _ = kcl.kcl_list(g2, 5, "degree", None)
+        g2.free()
+        te.append(time.perf_counter() - t)
+        if want and (c, c2, s, c3, c4, s2) != (want["count"], want["count"], want["checksum"],
+                                                 want["count"], want["count"], want["checksum"]):
+            raise AssertionError("C1: (%d, %d, %#x) differs from the oracle's (%d, %#x)" %
+                                 (c, c2, s, want["count"], want["checksum"]))
+    g.free()
+    med = statistics.median
+    return {"workload": "chung-lu-n10000-m50000-g2.5-20xK12 (seed 1), k=5, degree ordering",
+            "count": c, "checksum": "%#x" % s, "oracle_checked": bool(want),
+            "count_ms_median": 1e3 * med(tc), "list_ms_median": 1e3 * med(tl),
+            "e2e_load_count_list_ms_median": 1e3 * med(te), "repeats": repeats}
 
 
 def max_over_ranks(values, world):
@@ -804,6 +847,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-k6", action="store_true", help="skip the timed k = 6 calls")
+    ap.add_argument("--no-c1", action="store_true", help="skip the small Chung-Lu line")
     ap.add_argument("--form", default="single", choices=["single", "batch", "serve", "ablation"],
                     help="single: the R-MAT scale-20 line; batch / serve: the batched and "
                          "served workloads, each printing its own JSON line")

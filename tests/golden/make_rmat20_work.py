@@ -29,6 +29,7 @@ so that the oracle runs on every core; the count adds the Pre-List cliques
   "sample": {"roots": [...], "per_root": [...]} for a (k, ordering) whose
   full count is beyond the oracle.
 Usage: python tests/golden/make_rmat20_work.py [--checksum | --sample | --color | --degree] [k ...]
+       python tests/golden/make_rmat20_work.py --c1   (the small Chung-Lu workload, k = 5)
 (--color / --degree: counts and work of that ordering only.)
 """
 import json
@@ -189,8 +190,28 @@ def main_sample(ks):
         json.dump(dict(sorted(data.items())), f, indent=1)
 
 
+def main_c1():
+    """The small Chung-Lu workload (n = 10,000, 50,000 drawn pairs, exponent
+    2.5, 20 planted 12-cliques, seed 1) at k = 5: the oracle's count and
+    checksum, stored as "c1 k=5"."""
+    import kclgen
+    import oracle
+    rp, col = kclgen.chung_lu_planted_small(seed=1)
+    cnt, cks = oracle.plain(rp, col, 5)
+    data = {}
+    if os.path.exists(OUT):
+        with open(OUT) as f:
+            data = json.load(f)
+    data["c1 k=5"] = {"count": cnt, "checksum": cks, "n": len(rp) - 1, "undirected_edges": len(col) // 2}
+    with open(OUT, "w") as f:
+        json.dump(dict(sorted(data.items())), f, indent=1)
+    print("c1 k=5", cnt, hex(cks))
+
+
 def main():
     args = sys.argv[1:]
+    if args and args[0] == "--c1":
+        return main_c1()
     if args and args[0] == "--checksum":
         return main_checksum([int(a) for a in args[1:]] or [4])
     if args and args[0] == "--sample":
