@@ -768,6 +768,58 @@ def run_serve(args):
     return out
 
 
+def run_c3(args):
+    """The community workload at full size: Chung-Lu n = 4,000,000, 1.2e8
+    drawn pairs, exponent 2.1, expected degree capped at 40,000, plus 2,000
+    communities of 60-300 vertices at density 0.8 (seed 1), colour ordering
+    (BitCol) with Pre-Core and Pre-List; degree ordering (SDegree) beside it.
+    Every call runs under the library's time limit (--c3-limit-s, the
+    paper's "exceeds the time limit" outcome otherwise): counting at
+    k = 6, 8, 10, and listing k = 6 into a 4 GiB wrapping device ring."""
+    import torch
+
+    import kclgen
+    import paper_2203_13512_gb300 as kcl
+    t = time.perf_counter()
+    rp, col = kclgen.chung_lu_communities(seed=1)
+    gen_s = time.perf_counter() - t
+    g = kcl.kcl_load_csr(rp, col)
+    kcl.kcl_enable_timing(g, True)
+    kcl.kcl_set_time_limit(g, int(args.c3_limit_s * 1000))
+    ring = torch.empty(RING_BYTES // 4, dtype=torch.int32, device="cuda")
+    out = {"metric": "k-cliques/s, community workload (time-limited calls)", "unit": "k-cliques/s",
+           "higher_is_better": True, "n_gpus": 1,
+           "config": {"workload": "chung-lu-communities-n4e6", "n": len(rp) - 1,
+                      "undirected_edges": len(col) // 2, "limit_s": args.c3_limit_s,
+                      "generation_s": round(gen_s, 1)},
+           "data": "synthetic (seeded Chung-Lu generator, planted communities)", "calls": {}}
+    plan = [(6, "color", "count"), (6, "degree", "count"), (8, "color", "count"),
+            (10, "color", "count"), (6, "color", "list")]
+    for k, o, m in plan:
+        key = "k=%d %s %s" % (k, o, m)
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        try:
+            if m == "count":
+                c, s = kcl.kcl_count(g, k, o), None
+            else:
+                r = ring[: ring.numel() // k * k]
+                c, s, _, _ = kcl.kcl_list(g, k, o, r, wrap=True)
+            ms, la, cl = kcl.kcl_last_timing(g)
+            out["calls"][key] = {"count": c, "checksum": s, "ms": ms["total"],
+                                 "k_cliques_per_s": c / (ms["total"] / 1e3),
+                                 "stage_ms": {st: round(v, 2) for st, v in ms.items()}}
+        except kcl.KclError as e:
+            what = {kcl.KCL_ETIMEOUT: "exceeds the %g s limit" % args.c3_limit_s,
+                    kcl.KCL_EOVERFLOW: "count exceeds 2^64 - 1"}.get(e.status, str(e))
+            out["calls"][key] = {"result": what, "wall_s": round(time.perf_counter() - t, 1)}
+        print("c3 %s: %s" % (key, out["calls"][key]), file=sys.stderr, flush=True)
+    done = [v for v in out["calls"].values() if "count" in v]
+    out["value"] = (sum(v["count"] for v in done) / (sum(v["ms"] for v in done) / 1e3)) if done else None
+    g.free()
+    return out
+
+
 def run_ablation(args):
     """The preprocessing / pruning study, the NodeParallel / EdgeParallel study
     and the memory study on the bench graph (R-MAT scale 20): for k = 4, 5
@@ -848,7 +900,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-k6", action="store_true", help="skip the timed k = 6 calls")
     ap.add_argument("--no-c1", action="store_true", help="skip the small Chung-Lu line")
-    ap.add_argument("--form", default="single", choices=["single", "batch", "serve", "ablation"],
+    ap.add_argument("--c3-limit-s", type=float, default=60.0,
+                    help="time limit of each call of the community workload (--form c3)")
+    ap.add_argument("--form", default="single", choices=["single", "batch", "serve", "ablation", "c3"],
                     help="single: the R-MAT scale-20 line; batch / serve: the batched and "
                          "served workloads, each printing its own JSON line")
     ap.add_argument("--batch-graphs", type=int, default=512)
@@ -862,7 +916,8 @@ def main():
         profile_case(args.profile_case)
         return
     if args.form != "single":
-        res = {"batch": run_batch, "serve": run_serve, "ablation": run_ablation}[args.form](args)
+        res = {"batch": run_batch, "serve": run_serve, "ablation": run_ablation,
+               "c3": run_c3}[args.form](args)
         print(json.dumps(res))
         return
     world = int(os.environ.get("WORLD_SIZE", "1"))

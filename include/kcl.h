@@ -47,7 +47,7 @@ typedef enum {
     KCL_ENOMEM = 2,     /* device or host allocation failed */
     KCL_EOVERFLOW = 3,  /* the exact count does not fit in 64 bits */
     KCL_ETRUNC = 4,     /* listing: more cliques than ring capacity (wrap = 0) */
-    KCL_ETIMEOUT = 5,   /* a bounded device-side wait gave up */
+    KCL_ETIMEOUT = 5,   /* a bounded device-side wait gave up, or the time limit passed */
     KCL_ECUDA = 6,      /* a CUDA runtime call failed */
     KCL_EABORT = 7,     /* aborted by the caller */
     KCL_ELIMIT = 8,     /* a built-in size limit was exceeded (see kcl_strerror) */
@@ -240,6 +240,16 @@ kcl_status kcl_last_timing(const kcl_graph *g, kcl_timing *t);
  * the last kcl_count_batch call; *groups receives the number of groups. */
 kcl_status kcl_batch_enable_timing(kcl_batch *b, int enable);
 kcl_status kcl_batch_last_timing(const kcl_batch *b, kcl_timing *t, uint32_t *groups);
+
+/* Time limit of the listing stage of later kcl_count / kcl_list /
+ * kcl_count_per_root calls on g, in milliseconds (0 = none, the default).
+ * The paper runs every experiment under a wall-clock limit and reports
+ * "exceeds the limit" (Section IX); here the listing kernels stop taking
+ * roots and subtrees once the device's global timer passes the limit, and
+ * the call returns KCL_ETIMEOUT (its count is then incomplete and not
+ * returned).  The front end (Pre-Core, Pre-List, orientation) is not
+ * limited. */
+kcl_status kcl_set_time_limit(kcl_graph *g, uint64_t ms);
 
 /* Ablation switches (Section IX, the preprocessing and pruning studies): a
  * bitwise OR of

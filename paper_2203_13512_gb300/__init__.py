@@ -285,6 +285,16 @@ KCL_OPT_NO_PRELIST = 2
 KCL_OPT_NO_COLOR_PRUNE = 4
 
 
+_lib.kcl_set_time_limit.argtypes = [_P, _U64]
+_lib.kcl_set_time_limit.restype = _I
+
+
+def kcl_set_time_limit(g, ms):
+    """Time limit of the listing stage of later calls on g, in ms (0: none);
+    a call that exceeds it raises KclError with status KCL_ETIMEOUT."""
+    _check(_lib.kcl_set_time_limit(g.handle, int(ms)), "kcl_set_time_limit")
+
+
 def kcl_set_options(g, flags):
     """Ablation switches (KCL_OPT_* bits); results do not change."""
     _check(_lib.kcl_set_options(g.handle, int(flags)), "kcl_set_options")

@@ -215,6 +215,7 @@ struct FrontEnd {
 
 kcl_status status_from_device(uint32_t st) {
     if (st & DEV_ERR_INTERNAL) return KCL_ECUDA;
+    if (st & DEV_ERR_TIMEOUT) return KCL_ETIMEOUT;
     if (st & DEV_ERR_OUTDEG_LIMIT) return KCL_ELIMIT;
     if (st & DEV_ERR_OVERFLOW) return KCL_EOVERFLOW;
     if (st & DEV_ERR_INVALID_GRAPH) return KCL_EINVAL;
@@ -366,6 +367,7 @@ kcl_status run_call(kcl_graph *g, uint32_t k, kcl_ordering ord, const kcl_ring *
         la.wrap = ring->wrap;
     }
     T.begin(3);
+    if (fe.n_roots > 0) T.add(3, launch_set_deadline(w.res, g->time_limit_ms, g->stream));
     if (fe.n_roots > 0) {
         size_t arena = ord == KCL_ORDER_DEGREE
                            ? sdegree_arena_words(k, g->num_sms, fe.max_outdeg)
@@ -509,7 +511,7 @@ const char *kcl_strerror(kcl_status s) {
         case KCL_ENOMEM: return "out of memory";
         case KCL_EOVERFLOW: return "clique count exceeds 2^64-1";
         case KCL_ETRUNC: return "more cliques than ring capacity (output truncated)";
-        case KCL_ETIMEOUT: return "device wait timed out";
+        case KCL_ETIMEOUT: return "time limit exceeded or device wait timed out";
         case KCL_ECUDA: return "CUDA runtime error";
         case KCL_EABORT: return "aborted";
         case KCL_ELIMIT: return "root out-degree above the supported limit";
@@ -796,6 +798,12 @@ kcl_status kcl_last_timing(const kcl_graph *g, kcl_timing *t) {
         t->class_roots[c] = g->timing.class_roots[c];
         t->class_ms[c] = g->timing.class_ms[c];
     }
+    return KCL_OK;
+}
+
+kcl_status kcl_set_time_limit(kcl_graph *g, uint64_t ms) {
+    if (!g) return KCL_EINVAL;
+    g->time_limit_ms = ms;
     return KCL_OK;
 }
 

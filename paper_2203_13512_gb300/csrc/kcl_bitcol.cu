@@ -336,6 +336,7 @@ struct View {  // read-only view of a built subproblem, per warp
     const uint32_t *ids;
     uint32_t d, W, WP, ncol, u, k;
     uint32_t prune;  // 0: expand every candidate (ablation of Lemma 1)
+    unsigned long long deadline;  // time limit (global timer, ns; 0 = none)
 };
 
 // First candidate index at level l: the vertices of colour >= l (Lemma 1),
@@ -663,6 +664,7 @@ __device__ void dfs_child(const View &v, uint32_t p0, uint32_t *stack, const Emi
     __syncwarp();
     int depth = 1;
     while (depth >= 1) {
+        if (warp_past_deadline(v.deadline, res)) return;
         uint32_t *P = Pst + depth * W;
         uint32_t j = cur[depth];
         while (j < W && P[j] == 0) j++;
@@ -742,8 +744,10 @@ __global__ void __launch_bounds__(128, 8) k_bitcol_warp(uint32_t k, const uint32
     uint32_t *S = smem + (threadIdx.x >> 5) * per_warp;
     const Sub s = sub_ptrs(S, L, nullptr, nullptr);
     uint32_t *stack = S + L.total;
+    const unsigned long long deadline = __ldcg(&res->deadline_ns);
     unsigned long long cnt = 0, cks = 0;
     for (;;) {
+        if (warp_past_deadline(deadline, res)) break;
         uint32_t idx = 0;
         if (lane == 0) idx = atomicAdd(queue, 1u);
         idx = __shfl_sync(kFull, idx, 0);
@@ -758,7 +762,7 @@ __global__ void __launch_bounds__(128, 8) k_bitcol_warp(uint32_t k, const uint32
             __syncwarp();
         }
         const uint32_t uo = (LIST && em.idmap) ? em.idmap[u] : u;
-        View v{s.B, s.colp, s.start, s.ids, d, WT, L.WPB, s.meta[0], uo, k, em.prune};
+        View v{s.B, s.colp, s.start, s.ids, d, WT, L.WPB, s.meta[0], uo, k, em.prune, deadline};
         if (k == 3) {
             const uint32_t dw = (d + 31) >> 5;
             for (uint32_t t = lane; t < WT; t += 32)
@@ -819,21 +823,24 @@ __global__ void __launch_bounds__(NW * 32, (32 / NW > 0 ? 32 / NW : 1)) k_bitcol
     const Sub s = sub_ptrs(smem, L, Ag, Bg);
     uint32_t *stack = smem + L.total + warp * dfs_words(W, k);
     __shared__ int help_slot;  // -1: own root from the queue; else the slot of the root helped
+    const unsigned long long deadline = __ldcg(&res->deadline_ns);
     unsigned long long cnt = 0, cks = 0;
     bool queue_done = false;
     for (;;) {
-        if (threadIdx.x == 0) {
+        if (threadIdx.x == 0) {  // thread 0 alone reads the timer
+            if (!queue_done && past_deadline(deadline, res)) queue_done = true;
             root_idx = queue_done ? end - begin : atomicAdd(queue, 1u);
-            help_slot = -1;
+            help_slot = (queue_done && deadline && global_ns() > deadline) ? -2 : -1;
         }
         __syncthreads();
         uint32_t idx = root_idx;
+        const bool late = help_slot == -2;
         int helping = -1;
-        __syncthreads();  // every thread has read root_idx before it is rewritten
+        __syncthreads();  // every thread has read root_idx and help_slot before they are rewritten
         if (idx >= end - begin) {
             queue_done = true;
             // no root left: help the root with the most children left
-            if (!em.split || k == 3) break;
+            if (!em.split || k == 3 || late) break;
             if (warp == 0) {
                 uint32_t pos = 0;
                 const int j = split_pick(em.slots, gridDim.x, blockIdx.x, em.split, &pos);
@@ -854,7 +861,7 @@ __global__ void __launch_bounds__(NW * 32, (32 / NW > 0 ? 32 / NW : 1)) k_bitcol
             __syncthreads();
         }
         const uint32_t uo = (LIST && em.idmap) ? em.idmap[u] : u;
-        View v{s.B, s.colp, s.start, s.ids, d, W, L.WPB, s.meta[0], uo, k, em.prune};
+        View v{s.B, s.colp, s.start, s.ids, d, W, L.WPB, s.meta[0], uo, k, em.prune, deadline};
         if (k == 3) {
             const uint32_t dw = (d + 31) >> 5;
             for (uint32_t t = lane; t < W; t += 32)

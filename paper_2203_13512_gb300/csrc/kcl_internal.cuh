@@ -18,6 +18,7 @@ enum : uint32_t {
     DEV_ERR_OUTDEG_LIMIT = 1u << 1,
     DEV_ERR_OVERFLOW = 1u << 2,
     DEV_ERR_INTERNAL = 1u << 3,
+    DEV_ERR_TIMEOUT = 1u << 4,  // the call's time limit passed (kcl_set_time_limit)
 };
 
 // Result words written by the device and read back once per call.
@@ -36,6 +37,7 @@ struct DevResult {
     unsigned int remaining;          // vertices not yet peeled
     unsigned int n_clique_comps;     // components removed by Pre-List
     unsigned int pad;
+    unsigned long long deadline_ns;  // %globaltimer value after which listing stops (0: none)
 };
 
 // Control block of the single-launch degeneracy peel: grid barrier state,
@@ -123,6 +125,7 @@ struct kcl_graph {
     kcl::Timing timing;
     kcl_tuning tuning = {};  // listing-kernel knobs (results never depend on them)
     uint32_t options = 0;    // KCL_OPT_* ablation switches
+    uint64_t time_limit_ms = 0;  // listing-stage time limit (0: none)
 };
 
 namespace kcl {
@@ -245,6 +248,30 @@ __device__ __forceinline__ int split_pick(unsigned long long *slots, uint32_t ns
     }
     *pos = best_pos;
     return best_left ? (int)best : -1;
+}
+
+// ------------------------------------------------------------- time limit
+// The listing kernels stop taking work once the device's global timer passes
+// DevResult::deadline_ns (set when the listing stage starts; 0 = no limit)
+// and record DEV_ERR_TIMEOUT; the call then returns KCL_ETIMEOUT.
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ bool past_deadline(unsigned long long deadline, DevResult *res) {
+    if (!deadline || global_ns() <= deadline) return false;
+    atomicOr(&res->status, DEV_ERR_TIMEOUT);
+    return true;
+}
+
+// The same test taken once per warp (lane 0 reads the timer), so the warp
+// stays converged.
+__device__ __forceinline__ bool warp_past_deadline(unsigned long long deadline, DevResult *res) {
+    bool late = false;
+    if (deadline && (threadIdx.x & 31u) == 0) late = past_deadline(deadline, res);
+    return __shfl_sync(0xffffffffu, late, 0);
 }
 
 // Inclusive prefix sum over the 32 lanes of a warp (all lanes active).
@@ -385,6 +412,8 @@ int launch_roots(const kcl_graph *g, uint32_t k, Workspace &w, uint32_t max_outd
                  cudaStream_t s);
 int launch_exclusive_scan(const uint32_t *in, uint32_t *out, uint32_t n, uint32_t *block_tmp,
                           cudaStream_t s);
+// res->deadline_ns = now + limit_ms (or 0 when limit_ms is 0).
+int launch_set_deadline(DevResult *res, uint64_t limit_ms, cudaStream_t s);
 int launch_union_build(const BatchSrc *src, uint32_t G, uint32_t n_total, uint64_t *urp,
                        uint32_t *ucol, uint32_t *graph_of, uint32_t *idmap, cudaStream_t s);
 int launch_graph_sums(const BatchSrc *src, uint32_t G, const unsigned long long *vcount,

@@ -752,6 +752,15 @@ int launch_exclusive_scan(const uint32_t *in, uint32_t *out, uint32_t n, uint32_
     return l + 1;
 }
 
+__global__ void k_set_deadline(DevResult *res, unsigned long long limit_ns) {
+    res->deadline_ns = limit_ns ? global_ns() + limit_ns : 0ull;
+}
+
+int launch_set_deadline(DevResult *res, uint64_t limit_ms, cudaStream_t s) {
+    k_set_deadline<<<1, 1, 0, s>>>(res, (unsigned long long)limit_ms * 1000000ull);
+    return 1;
+}
+
 int launch_validate(const kcl_graph *g, DevResult *res, cudaStream_t s) {
     int grid = grid_for((uint64_t)g->n * 32, kBlock, g->num_sms, 32);
     k_validate<<<grid, kBlock, 0, s>>>(g->n, g->nnz, g->rp, g->col, res);

@@ -140,8 +140,10 @@ __device__ void sdegree_root(uint32_t u, uint32_t k, uint32_t D, const uint32_t 
     for (uint32_t i = lane; i < d; i += 32) lists[i] = oadj[base + i];
     if (lane == 0) { pos[0] = 0; size[0] = d; path[0] = u; }
     __syncwarp();
+    const unsigned long long deadline = __ldcg(&res->deadline_ns);
     int depth = 0;
     while (depth >= 0) {
+        if (warp_past_deadline(deadline, res)) return;
         const uint32_t l = k - 1 - (uint32_t)depth;
         const uint32_t *C = lists + depth * D;
         const uint32_t nC = size[depth];
@@ -326,6 +328,7 @@ struct LView {
     const uint16_t *ladj;  // reduced out-lists, ascending local indices, padded
     uint32_t d, u, k;
     uint32_t gallop;       // leaf form threshold (kcl_tuning.sdegree_gallop); 0 = merges
+    unsigned long long deadline;  // time limit (global timer, ns; 0 = none)
     __device__ __forceinline__ uint32_t deg(uint32_t i) const { return len[i]; }
     __device__ __forceinline__ const uint16_t *list(uint32_t i) const { return ladj + lofs[i]; }
 };
@@ -531,6 +534,7 @@ __device__ void ldfs_child(const LView &v, uint32_t p0, const LStack &st, const 
     __syncwarp();
     int depth = 1;
     while (depth >= 1) {
+        if (warp_past_deadline(v.deadline, res)) return;
         const uint32_t pp = st.ppos[depth];
         if (pp >= st.npend[depth]) { depth--; continue; }
         const uint32_t pos = st.pend[(depth - 1) * cap + pp];
@@ -571,6 +575,7 @@ struct BView {
     const uint32_t *R;    // bit-rows, stride WP words
     const uint32_t *ids;  // local index -> output id
     uint32_t d, W, WP, u, k;  // W: words per row
+    unsigned long long deadline;  // time limit (global timer, ns; 0 = none)
 };
 
 __host__ __device__ inline uint32_t bstack_words(uint32_t W, uint32_t k) {
@@ -811,6 +816,7 @@ __device__ void bdfs_child(const BView &v, uint32_t p0, uint32_t *stack, const E
     __syncwarp();
     int depth = 1;
     while (depth >= 1) {
+        if (warp_past_deadline(v.deadline, res)) return;
         uint32_t *P = Pst + depth * W;
         uint32_t j = cur[depth];
         while (j < W && P[j] == 0) j++;
@@ -971,9 +977,10 @@ __device__ void sdegree_root_local(uint32_t u, uint32_t k, uint32_t D, const uin
         for (uint32_t i = lane; i < d; i += 32) rs[i] = em.idmap[rs[i]];
         __syncwarp();
     }
-    const LView v{rs, lofs, len, ladj, d, (LIST && em.idmap) ? em.idmap[u] : u, k, gallop};
+    const LView v{rs, lofs, len, ladj, d, (LIST && em.idmap) ? em.idmap[u] : u, k, gallop,
+                  __ldcg(&res->deadline_ns)};
     if (bitrows) {
-        const BView bv{bits, rs, d, (d + 31) >> 5, L.WPD, v.u, k};
+        const BView bv{bits, rs, d, (d + 31) >> 5, L.WPD, v.u, k, v.deadline};
         for (uint32_t w = 0; w < d; w++)
             if (v.deg(w) + 2 >= k) bdfs_child<LIST>(bv, w, S + L.STACK, em, res, cnt, cks);
         return;
@@ -1074,19 +1081,22 @@ __global__ void __launch_bounds__(512) k_sdegree_cta(uint32_t k, uint32_t D, con
     __shared__ int help_slot;  // -1: own root from the queue; else the slot of the root helped
     unsigned long long *my_slot = em.slots + blockIdx.x;
     bool queue_done = false;
+    const unsigned long long deadline = __ldcg(&res->deadline_ns);
     for (;;) {
-        if (tid == 0) {
+        if (tid == 0) {  // thread 0 alone reads the timer
+            if (!queue_done && past_deadline(deadline, res)) queue_done = true;
             meta[15] = queue_done ? end - begin : atomicAdd(queue, 1u);
-            help_slot = -1;
+            help_slot = (queue_done && deadline && global_ns() > deadline) ? -2 : -1;
         }
         __syncthreads();
         uint32_t idx = meta[15];
+        const bool late = help_slot == -2;
         int helping = -1;
-        __syncthreads();  // every thread has read meta[15] before it is rewritten
+        __syncthreads();  // every thread has read meta[15] and help_slot before they are rewritten
         if (idx >= end - begin) {
             queue_done = true;
             // no root left: help the root with the most children left
-            if (!em.split || k == 3) break;
+            if (!em.split || k == 3 || late) break;
             if (warp == 0) {
                 uint32_t pos = 0;
                 const int j = split_pick(em.slots, gridDim.x, blockIdx.x, em.split, &pos);
@@ -1258,7 +1268,8 @@ __global__ void __launch_bounds__(512) k_sdegree_cta(uint32_t k, uint32_t D, con
         if (nw_dfs == 0 && tid == 0) atomicOr(&res->status, DEV_ERR_INTERNAL);  // no stack fits
         if (LIST && em.idmap)  // output ids (batched unions map back to each graph's ids)
             for (uint32_t i = tid; i < d; i += nth) rs[i] = em.idmap[rs[i]];
-        const LView v{rs, lofs, len, ladj, d, (LIST && em.idmap) ? em.idmap[u] : u, k, gallop};
+        const LView v{rs, lofs, len, ladj, d, (LIST && em.idmap) ? em.idmap[u] : u, k, gallop,
+                  __ldcg(&res->deadline_ns)};
         const uint32_t cap = meta[3] ? meta[3] : 1;
         // ---- first-level children (|L(w)| >= k-2), longest lists first
         if (k > 3 && warp == 0) {
@@ -1290,7 +1301,7 @@ __global__ void __launch_bounds__(512) k_sdegree_cta(uint32_t k, uint32_t D, con
             __syncthreads();
         }
         if (bitrows && warp < nw_dfs) {
-            const BView bv{smem + L.total, rs, d, meta[10], meta[11], v.u, k};
+            const BView bv{smem + L.total, rs, d, meta[10], meta[11], v.u, k, deadline};
             uint32_t *stack = smem + L.total + meta[7] + warp * sw;
             const uint32_t n0 = meta[8];
             for (;;) {
@@ -1360,8 +1371,10 @@ __global__ void __launch_bounds__(128) k_sdegree(uint32_t k, uint32_t D, const u
     const uint32_t wib = threadIdx.x >> 5;
     uint32_t *S = GLOBAL ? arena + (size_t)(blockIdx.x * (blockDim.x >> 5) + wib) * words_per_warp
                          : smem + wib * words_per_warp;
+    const unsigned long long deadline = __ldcg(&res->deadline_ns);
     unsigned long long cnt = 0, cks = 0;
     for (;;) {
+        if (warp_past_deadline(deadline, res)) break;
         uint32_t idx = 0;
         if (lane == 0) idx = atomicAdd(queue, 1u);
         idx = __shfl_sync(kFull, idx, 0);

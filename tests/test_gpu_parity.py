@@ -589,3 +589,24 @@ def test_work_splitting_keeps_results(kcl, split):
         assert (c, s, w, trunc) == (ref_c, ref_s, ref_c, False)
         got = ring[: w * 4].cpu().numpy().astype(np.uint32).reshape(-1, 4)
         assert np.array_equal(got[np.lexsort(got.T[::-1])], want), o
+
+
+def test_time_limit_stops_a_long_call(kcl):
+    """kcl_set_time_limit: a call whose listing stage outlasts the limit
+    returns KCL_ETIMEOUT (R-MAT scale 16, k = 7: seconds of work against a
+    1 ms limit), the handle stays usable, and a generous limit leaves the
+    results unchanged."""
+    rp, col = kclgen.rmat20(seed=1, scale=16)
+    g = kcl.kcl_load_csr(rp, col)
+    ref = kcl.kcl_count(g, 5, "color")
+    for o in ORDS:
+        kcl.kcl_set_time_limit(g, 1)
+        with pytest.raises(kcl.KclError) as e:
+            kcl.kcl_count(g, 7, o)
+        assert e.value.status == kcl.KCL_ETIMEOUT
+        with pytest.raises(kcl.KclError):
+            kcl.kcl_list(g, 7, o, None)
+        kcl.kcl_set_time_limit(g, 600_000)
+        assert kcl.kcl_count(g, 5, o) == ref
+        kcl.kcl_set_time_limit(g, 0)
+        assert kcl.kcl_count(g, 5, o) == ref
