@@ -132,6 +132,18 @@ kcl_status kcl_list(kcl_graph *g, uint32_t k, kcl_ordering ord, const kcl_ring *
 kcl_status kcl_count_per_root(kcl_graph *g, uint32_t k, kcl_ordering ord, uint64_t *per_root,
                               uint64_t *count, uint64_t *prelist_count);
 
+/* Per-root counts of the given roots only, for checking large graphs root by
+ * root against an independent implementation (whose full count may be out of
+ * reach).  The front end runs on the whole graph; then only the roots listed
+ * in `roots` (host uint32[n_roots], vertex ids < n; vertices that are not
+ * roots under `ord` -- removed by Pre-Core or Pre-List, or d+ < k-1 -- are
+ * skipped) are expanded.  per_root: device uint64[n], overwritten as in
+ * kcl_count_per_root (zero for every other vertex); *count receives their
+ * sum (Pre-List cliques are not included).  Errors: those of kcl_count,
+ * KCL_EINVAL for an id >= n. */
+kcl_status kcl_count_roots(kcl_graph *g, uint32_t k, kcl_ordering ord, const uint32_t *roots,
+                           uint32_t n_roots, uint64_t *per_root, uint64_t *count);
+
 /* Intermediate results of the front end, for stage-by-stage checks.
  * Any pointer may be NULL.  Host buffers of n elements:
  *   alive_core:  1 iff the vertex survives Pre-Core (the (k-1)-core, Alg. 3)

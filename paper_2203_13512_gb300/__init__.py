@@ -243,6 +243,23 @@ def kcl_count_per_root(g, k, ordering, per_root):
     return int(c.value), int(p.value)
 
 
+_lib.kcl_count_roots.argtypes = [_P, _U32, _I, _P, _U32, _P, ctypes.POINTER(_U64)]
+_lib.kcl_count_roots.restype = _I
+
+
+def kcl_count_roots(g, k, ordering, roots, per_root):
+    """Per-root counts of the given roots only (numpy uint32 ids) into
+    ``per_root`` (CUDA int64 tensor, n entries); returns their sum."""
+    r = np.ascontiguousarray(roots, dtype=np.uint32)
+    if per_root.numel() < g.n:
+        raise ValueError("per_root too small")
+    c = ctypes.c_uint64()
+    _check(_lib.kcl_count_roots(g.handle, k, _ord(ordering), r.ctypes.data if r.size else None,
+                                r.size, ctypes.c_void_p(per_root.data_ptr()), ctypes.byref(c)),
+           "kcl_count_roots")
+    return int(c.value)
+
+
 def kcl_stage_info(g, k, ordering):
     """Front-end intermediates as numpy arrays: alive_core, alive_final,
     outdeg, key, prelist_count, max_outdeg."""

@@ -644,6 +644,42 @@ kcl_status kcl_count_per_root(kcl_graph *g, uint32_t k, kcl_ordering ord, uint64
     return total_count(g->ws.h_res, count);
 }
 
+kcl_status kcl_count_roots(kcl_graph *g, uint32_t k, kcl_ordering ord, const uint32_t *roots,
+                           uint32_t n_roots, uint64_t *per_root, uint64_t *count) {
+    if (!per_root || !count || (n_roots && !roots)) return KCL_EINVAL;
+    KCL_TRY(check_args(g, k, ord));
+    for (uint32_t i = 0; i < n_roots; i++)
+        if (roots[i] >= g->n) return KCL_EINVAL;
+    if (cudaSetDevice(g->device) != cudaSuccess) return KCL_ECUDA;
+    std::vector<uint8_t> mask((size_t)g->n + 1, 0);
+    for (uint32_t i = 0; i < n_roots; i++) mask[roots[i]] = 1;
+    uint8_t *d_mask = nullptr;
+    if (cudaMalloc((void **)&d_mask, mask.size()) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return KCL_ENOMEM;
+    }
+    kcl_status st = KCL_OK;
+    if (cudaMemcpyAsync(d_mask, mask.data(), mask.size(), cudaMemcpyHostToDevice, g->stream) != cudaSuccess ||
+        cudaMemsetAsync(per_root, 0, (size_t)g->n * sizeof(uint64_t), g->stream) != cudaSuccess) {
+        (void)cudaGetLastError();
+        st = KCL_ECUDA;
+    }
+    if (st == KCL_OK) {
+        g->ws.root_mask = d_mask;
+        st = run_call(g, k, ord, nullptr, false, reinterpret_cast<unsigned long long *>(per_root));
+        g->ws.root_mask = nullptr;
+    }
+    if (st == KCL_OK) {
+        const DevResult *r = g->ws.h_res;
+        if (r->count_carry) st = KCL_EOVERFLOW;
+        else *count = r->count;
+    }
+    cudaStreamSynchronize(g->stream);
+    (void)cudaGetLastError();
+    cudaFree(d_mask);
+    return st;
+}
+
 kcl_status kcl_stage_info(kcl_graph *g, uint32_t k, kcl_ordering ord, uint8_t *alive_core,
                           uint8_t *alive_final, uint32_t *outdeg, uint32_t *key,
                           uint64_t *prelist_count, uint32_t *max_outdeg) {

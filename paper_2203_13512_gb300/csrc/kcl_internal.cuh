@@ -93,6 +93,7 @@ struct Workspace {
     unsigned long long *vcount_pre = nullptr;  // batch: Pre-List counts by component root
     unsigned long long *vcks_pre = nullptr;    // batch: Pre-List checksums by component root
     const uint32_t *idmap = nullptr;           // batch: union vertex -> graph's own id
+    const uint8_t *root_mask = nullptr;        // kcl_count_roots: only these roots (null: all)
     uint32_t n_cap = 0;
     uint64_t nnz_cap = 0;
 };

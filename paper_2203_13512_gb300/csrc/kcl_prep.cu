@@ -580,11 +580,11 @@ __global__ void k_outfill(uint32_t n, const uint64_t *__restrict__ rp, const uin
 // out-degree order by a counting sort: hist index = max_outdeg - d+.
 __global__ void k_root_hist(uint32_t n, uint32_t k, const uint8_t *__restrict__ alive,
                             const uint32_t *__restrict__ outdeg, uint32_t max_outdeg, uint32_t *hist,
-                            DevResult *res) {
+                            const uint8_t *__restrict__ mask, DevResult *res) {
     uint32_t cnt = 0;
     for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
         uint32_t d = outdeg[v];
-        if (alive[v] && d + 1 >= k) {
+        if (alive[v] && d + 1 >= k && (!mask || mask[v])) {
             atomicAdd(&hist[max_outdeg - d], 1u);
             cnt++;
         }
@@ -595,10 +595,11 @@ __global__ void k_root_hist(uint32_t n, uint32_t k, const uint8_t *__restrict__ 
 
 __global__ void k_root_scatter(uint32_t n, uint32_t k, const uint8_t *__restrict__ alive,
                                const uint32_t *__restrict__ outdeg, uint32_t max_outdeg,
-                               const uint32_t *__restrict__ offs, uint32_t *fill, uint32_t *roots) {
+                               const uint32_t *__restrict__ offs, uint32_t *fill,
+                               const uint8_t *__restrict__ mask, uint32_t *roots) {
     for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
         uint32_t d = outdeg[v];
-        if (alive[v] && d + 1 >= k) {
+        if (alive[v] && d + 1 >= k && (!mask || mask[v])) {
             uint32_t h = max_outdeg - d;
             roots[offs[h] + atomicAdd(&fill[h], 1u)] = v;
         }
@@ -907,10 +908,10 @@ int launch_roots(const kcl_graph *g, uint32_t k, Workspace &w, uint32_t max_outd
     uint32_t *limits = w.hist + 3 * (H + 1);
     cudaMemsetAsync(w.hist, 0, 3 * (H + 1) * sizeof(uint32_t), s);
     cudaMemcpyAsync(limits, class_limits, n_classes * sizeof(uint32_t), cudaMemcpyHostToDevice, s);
-    k_root_hist<<<grid, kBlock, 0, s>>>(g->n, k, w.alive, w.outdeg, max_outdeg, hist, w.res);
+    k_root_hist<<<grid, kBlock, 0, s>>>(g->n, k, w.alive, w.outdeg, max_outdeg, hist, w.root_mask, w.res);
     int l = 1 + launch_exclusive_scan(hist, offs, H + 1, w.scan_tmp, s);
     k_root_scatter<<<grid, kBlock, 0, s>>>(g->n, k, w.alive, w.outdeg, max_outdeg, offs, fill,
-                                           w.roots);
+                                           w.root_mask, w.roots);
     // class bounds into the tail of hist; n_roots = offs[H]
     uint32_t *cb = w.hist + 3 * (H + 1) + 64;
     k_class_bounds<<<1, 64, 0, s>>>(offs, max_outdeg, limits, n_classes, 0, cb);
