@@ -619,9 +619,11 @@ def run_reference(args, rank, world):
 def run_batch(args):
     """The batched workload: graph i = kclgen.batch_graph(i) (n log-uniform in
     [50, 20000], mean degree 4-40, exponent 2.3, 0-5 planted cliques of size
-    8-16, k uniform in 3..9), count + checksum per graph, both orderings.
-    Compares one kcl_count_batch call with one library call per graph on the
-    same resident graphs; results must be identical."""
+    8-16, k uniform in 3..9), count + checksum per graph, both orderings as two
+    sweeps.  Compares one kcl_count_batch call (per ordering: every graph in
+    one disjoint union with its own k, one pass of the pipeline) with one
+    library call per graph on the same resident graphs; results must be
+    identical."""
     import torch
 
     import kclgen
@@ -652,6 +654,7 @@ def run_batch(args):
             return list(zip(c, s))
 
         ref = per_graph()  # warm-up (allocates each graph's scratch)
+        print("batch %s: warm-up per-graph pass done" % o, file=sys.stderr, flush=True)
         got = batched()
         assert got == ref, "batched results differ from per-graph results"
         torch.cuda.synchronize()
@@ -663,6 +666,7 @@ def run_batch(args):
         batched()
         torch.cuda.synchronize()
         t_bat = time.perf_counter() - t
+        print("batch %s: per-graph %.2f s, batched %.2f s" % (o, t_per, t_bat), file=sys.stderr, flush=True)
         n_cl = sum(c for c, _ in ref)
         out["orderings"][o] = {"per_graph_s": round(t_per, 4), "batched_s": round(t_bat, 4),
                                "per_graph_graphs_per_s": G / t_per, "batched_graphs_per_s": G / t_bat,
@@ -905,7 +909,7 @@ def main():
     ap.add_argument("--form", default="single", choices=["single", "batch", "serve", "ablation", "c3"],
                     help="single: the R-MAT scale-20 line; batch / serve: the batched and "
                          "served workloads, each printing its own JSON line")
-    ap.add_argument("--batch-graphs", type=int, default=512)
+    ap.add_argument("--batch-graphs", type=int, default=2048)
     ap.add_argument("--serve-queries", type=int, default=2000)
     ap.add_argument("--serve-rates", type=float, nargs="+", default=[50.0, 150.0, 1000.0])
     ap.add_argument("--profile-case", default=None,

@@ -174,10 +174,13 @@ kcl_status kcl_root_colouring(kcl_graph *g, uint32_t k, uint32_t root, uint32_t 
  * A kcl_batch owns device scratch that is reused across calls; create it on
  * the device and stream the batch's graphs live on.
  * kcl_count_batch: gs[i] (loaded graphs, same device), ks[i] in [3,
- *   KCL_MAX_K], ords[i] per graph.  Graphs that share (k, ordering) are joined
- *   as one disjoint union on the device and counted by a single pass of the
- *   pipeline (Algorithms 3-6); each root's count is attributed to its vertex
- *   and summed per graph.  counts: host uint64[G], receives each graph's exact
+ *   KCL_MAX_K], ords[i] per graph.  The graphs of each ordering are joined as
+ *   one disjoint union on the device, each vertex keeping the k of its graph,
+ *   and counted by a single pass of the pipeline (Algorithms 3-6: Pre-Core
+ *   and Pre-List with each graph's k, one listing launch per out-degree class
+ *   whose persistent CTAs pull the roots of every graph from one queue); each
+ *   root's count is attributed to its vertex and summed per graph.  counts:
+ *   host uint64[G], receives each graph's exact
  *   k-clique count.  checksums: host uint64[G] or NULL; when given, each
  *   graph's listing checksum (as kcl_list) is computed too.
  * Errors: KCL_EINVAL, KCL_ENOMEM, KCL_ECUDA, KCL_ELIMIT (union beyond 2^32

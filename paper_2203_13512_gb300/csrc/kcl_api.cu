@@ -408,6 +408,7 @@ struct kcl_batch {
     uint32_t n_cap = 0;
     uint64_t nnz_cap = 0;
     uint32_t *graph_of = nullptr, *idmap = nullptr;
+    uint8_t *kmap = nullptr;  // union vertex -> k of its graph
     unsigned long long *vcount = nullptr, *vcks = nullptr;
     unsigned long long *gcount = nullptr, *gcks = nullptr;
     BatchSrc *d_src = nullptr;
@@ -429,6 +430,7 @@ kcl_status batch_reserve(kcl_batch *b, uint32_t n, uint64_t nnz, uint32_t G) {
         KCL_TRY(dev_alloc(&ug->col, ec ? ec : 1));
         KCL_TRY(dev_alloc(&b->graph_of, (size_t)nc + 1));
         KCL_TRY(dev_alloc(&b->idmap, (size_t)nc + 1));
+        KCL_TRY(dev_alloc(&b->kmap, (size_t)nc + 1));
         KCL_TRY(dev_alloc(&b->vcount, (size_t)nc + 1));
         KCL_TRY(dev_alloc(&b->vcks, (size_t)nc + 1));
         b->n_cap = nc;
@@ -443,25 +445,32 @@ kcl_status batch_reserve(kcl_batch *b, uint32_t n, uint64_t nnz, uint32_t G) {
     return KCL_OK;
 }
 
-// One (k, ordering) group of a batch.
-kcl_status batch_group(kcl_batch *b, kcl_graph *const *gs, const std::vector<uint32_t> &idx, uint32_t k,
-                       kcl_ordering ord, bool listing, uint64_t *counts, uint64_t *checksums) {
+// One ordering's group of a batch: its graphs, each with its own k, joined
+// as one disjoint union and run through one pass of the pipeline (the union's
+// k map gives every vertex the k of its graph; kernels are laid out for the
+// group's largest k).
+kcl_status batch_group(kcl_batch *b, kcl_graph *const *gs, const uint32_t *ks,
+                       const std::vector<uint32_t> &idx, kcl_ordering ord, bool listing,
+                       uint64_t *counts, uint64_t *checksums) {
     const uint32_t G = (uint32_t)idx.size();
     b->h_src.resize(G);
     uint64_t voff = 0, eoff = 0;
+    uint32_t kmax = 3;
     for (uint32_t i = 0; i < G; i++) {
         const kcl_graph *g = gs[idx[i]];
-        b->h_src[i] = BatchSrc{g->rp, g->col, g->n, (uint32_t)voff, g->nnz, eoff};
+        b->h_src[i] = BatchSrc{g->rp, g->col, g->n, (uint32_t)voff, g->nnz, eoff, ks[idx[i]], 0u};
         voff += g->n;
         eoff += g->nnz;
+        kmax = std::max(kmax, ks[idx[i]]);
     }
+    const uint32_t k = kmax;
     if (voff > 0xFFFFFFF0ull || eoff / 2 > 0xFFFFFFF0ull) return KCL_ELIMIT;
     const uint32_t n = (uint32_t)voff;
     KCL_TRY(batch_reserve(b, n, eoff, G));
     kcl_graph *ug = b->ug;
     cudaStream_t s = b->stream;
     KCL_CK(cudaMemcpyAsync(b->d_src, b->h_src.data(), G * sizeof(BatchSrc), cudaMemcpyHostToDevice, s));
-    launch_union_build(b->d_src, G, n, ug->rp, ug->col, b->graph_of, b->idmap, s);
+    launch_union_build(b->d_src, G, n, ug->rp, ug->col, b->graph_of, b->idmap, b->kmap, s);
     ug->n = n;
     ug->nnz = eoff;
     ug->stream = s;
@@ -471,10 +480,12 @@ kcl_status batch_group(kcl_batch *b, kcl_graph *const *gs, const std::vector<uin
     ug->ws.vcount_pre = b->vcount;
     ug->ws.vcks_pre = listing ? b->vcks : nullptr;
     ug->ws.idmap = b->idmap;
+    ug->ws.kmap = b->kmap;
     kcl_status st = n ? run_call(ug, k, ord, nullptr, listing, b->vcount, b->vcks, b->idmap) : KCL_OK;
     ug->ws.vcount_pre = nullptr;
     ug->ws.vcks_pre = nullptr;
     ug->ws.idmap = nullptr;
+    ug->ws.kmap = nullptr;
     if (st != KCL_OK) return st;
     if (ug->timing.enabled && n)
         for (int i = 0; i < KCL_NUM_STAGES; i++) {
@@ -764,7 +775,7 @@ void kcl_batch_free(kcl_batch *b) {
     if (b->stream) cudaStreamSynchronize(b->stream);
     else cudaDeviceSynchronize();
     (void)cudaGetLastError();
-    void *ptrs[] = {b->graph_of, b->idmap, b->vcount, b->vcks, b->gcount, b->gcks, b->d_src};
+    void *ptrs[] = {b->graph_of, b->idmap, b->kmap, b->vcount, b->vcks, b->gcount, b->gcks, b->d_src};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     kcl_free_graph(b->ug);
@@ -775,18 +786,18 @@ kcl_status kcl_count_batch(kcl_batch *b, kcl_graph *const *gs, const uint32_t *k
                            const kcl_ordering *ords, uint32_t G, uint64_t *counts,
                            uint64_t *checksums) {
     if (!b || (G && (!gs || !ks || !ords || !counts))) return KCL_EINVAL;
-    std::map<std::pair<uint32_t, int>, std::vector<uint32_t>> groups;
+    std::map<int, std::vector<uint32_t>> groups;  // by ordering; k varies within a group
     for (uint32_t i = 0; i < G; i++) {
         if (!gs[i] || gs[i]->device != b->device) return KCL_EINVAL;
         KCL_TRY(check_args(gs[i], ks[i], ords[i]));
-        groups[{ks[i], (int)ords[i]}].push_back(i);
+        groups[(int)ords[i]].push_back(i);
     }
     if (cudaSetDevice(b->device) != cudaSuccess) return KCL_ECUDA;
     b->timing = kcl_timing{};
     b->groups = 0;
     for (auto &kv : groups)
-        KCL_TRY(batch_group(b, gs, kv.second, kv.first.first, (kcl_ordering)kv.first.second,
-                            checksums != nullptr, counts, checksums));
+        KCL_TRY(batch_group(b, gs, ks, kv.second, (kcl_ordering)kv.first, checksums != nullptr, counts,
+                            checksums));
     return KCL_OK;
 }
 

@@ -328,6 +328,7 @@ struct Emit {
     uint32_t dfs_warps;            // CTA form: warps walking the children (0 = all)
     unsigned long long *slots;     // CTA form: work-splitting slots (one per CTA)
     uint32_t split;                // CTA form: help a root with >= split children left (0 = off)
+    const uint8_t *kmap;           // batches: k of each root's graph (null: the launch's k)
 };
 
 struct View {  // read-only view of a built subproblem, per warp
@@ -731,7 +732,7 @@ __device__ uint32_t root_children(const View &v, const Sub &s) {
 // --------------------------------------------------------------- kernels
 // Warp per root: subproblem and stack in this warp's slice of shared memory.
 template <int WT, bool LIST>
-__global__ void __launch_bounds__(128, 8) k_bitcol_warp(uint32_t k, const uint32_t *__restrict__ optr,
+__global__ void __launch_bounds__(128, 8) k_bitcol_warp(uint32_t kmax, const uint32_t *__restrict__ optr,
                                                     const uint32_t *__restrict__ oadj,
                                                     const uint32_t *__restrict__ roots,
                                                     uint32_t begin, uint32_t end, unsigned *queue,
@@ -740,7 +741,7 @@ __global__ void __launch_bounds__(128, 8) k_bitcol_warp(uint32_t k, const uint32
     extern __shared__ uint32_t smem[];
     const unsigned lane = lane_id();
     const SubLay L = sub_layout(WT, false, false);
-    const uint32_t per_warp = L.total + dfs_words(WT, k);
+    const uint32_t per_warp = L.total + dfs_words(WT, kmax);  // stacks for the largest k
     uint32_t *S = smem + (threadIdx.x >> 5) * per_warp;
     const Sub s = sub_ptrs(S, L, nullptr, nullptr);
     uint32_t *stack = S + L.total;
@@ -753,6 +754,7 @@ __global__ void __launch_bounds__(128, 8) k_bitcol_warp(uint32_t k, const uint32
         idx = __shfl_sync(kFull, idx, 0);
         if (idx >= end - begin) break;
         const uint32_t u = roots[begin + idx];
+        const uint32_t k = em.kmap ? (uint32_t)em.kmap[u] : kmax;
         const uint32_t base = optr[u], d = optr[u + 1] - base;
         const unsigned long long before = cnt;
         const unsigned long long before_cks = cks;
@@ -801,7 +803,7 @@ __global__ void __launch_bounds__(128, 8) k_bitcol_warp(uint32_t k, const uint32
 // children are handed out to the warps, heaviest first.
 // At least 1024 threads per SM (two 512-thread CTAs): at most 64 registers.
 template <int NW, bool LIST, bool AG, bool BG>
-__global__ void __launch_bounds__(NW * 32, (32 / NW > 0 ? 32 / NW : 1)) k_bitcol_cta(uint32_t k, uint32_t W, uint32_t D,
+__global__ void __launch_bounds__(NW * 32, (32 / NW > 0 ? 32 / NW : 1)) k_bitcol_cta(uint32_t kmax, uint32_t W, uint32_t D,
                                                        const uint32_t *__restrict__ optr,
                                                        const uint32_t *__restrict__ oadj,
                                                        const uint32_t *__restrict__ roots,
@@ -821,7 +823,7 @@ __global__ void __launch_bounds__(NW * 32, (32 / NW > 0 ? 32 / NW : 1)) k_bitcol
     uint32_t *Ag = AG ? slice : nullptr;
     uint32_t *Bg = BG ? slice + (AG ? rows_a : 0) : nullptr;
     const Sub s = sub_ptrs(smem, L, Ag, Bg);
-    uint32_t *stack = smem + L.total + warp * dfs_words(W, k);
+    uint32_t *stack = smem + L.total + warp * dfs_words(W, kmax);  // stacks for the largest k
     __shared__ int help_slot;  // -1: own root from the queue; else the slot of the root helped
     const unsigned long long deadline = __ldcg(&res->deadline_ns);
     unsigned long long cnt = 0, cks = 0;
@@ -840,7 +842,7 @@ __global__ void __launch_bounds__(NW * 32, (32 / NW > 0 ? 32 / NW : 1)) k_bitcol
         if (idx >= end - begin) {
             queue_done = true;
             // no root left: help the root with the most children left
-            if (!em.split || k == 3 || late) break;
+            if (!em.split || kmax == 3 || late) break;
             if (warp == 0) {
                 uint32_t pos = 0;
                 const int j = split_pick(em.slots, gridDim.x, blockIdx.x, em.split, &pos);
@@ -852,6 +854,7 @@ __global__ void __launch_bounds__(NW * 32, (32 / NW > 0 ? 32 / NW : 1)) k_bitcol
             if (helping < 0 || idx >= end - begin) break;
         }
         const uint32_t u = roots[begin + idx];
+        const uint32_t k = em.kmap ? (uint32_t)em.kmap[u] : kmax;
         const uint32_t base = optr[u], d = optr[u + 1] - base;
         const unsigned long long before = cnt;
         const unsigned long long before_cks = cks;
@@ -1067,7 +1070,7 @@ int launch_bitcol(const kcl_graph *g, uint32_t k, Workspace &w, const uint32_t *
                   int n_classes, const ListArgs &la, cudaStream_t s) {
     // class c covers root positions [class_begin[c], c ? class_begin[c-1] : n_roots)
     Emit em{la.ring, la.capacity, la.wrap, la.per_root_cks, la.idmap,
-            (g->options & KCL_OPT_NO_COLOR_PRUNE) ? 0u : 1u, 0u, w.slots, 0u};
+            (g->options & KCL_OPT_NO_COLOR_PRUNE) ? 0u : 1u, 0u, w.slots, 0u, w.kmap};
     int launches = 0;
     cudaMemsetAsync(w.queue, 0, 64 * sizeof(unsigned), s);
     for (int c = 0; c < n_classes; c++) {

@@ -60,6 +60,8 @@ struct BatchSrc {
     uint32_t voff;
     uint64_t nnz;
     uint64_t eoff;
+    uint32_t k;     // the graph's k (written to the union's k map)
+    uint32_t pad;
 };
 
 // Workspace owned by a graph, grown on demand and reused across calls.
@@ -94,6 +96,7 @@ struct Workspace {
     unsigned long long *vcks_pre = nullptr;    // batch: Pre-List checksums by component root
     const uint32_t *idmap = nullptr;           // batch: union vertex -> graph's own id
     const uint8_t *root_mask = nullptr;        // kcl_count_roots: only these roots (null: all)
+    const uint8_t *kmap = nullptr;             // batch: union vertex -> k of its graph (null: one k)
     uint32_t n_cap = 0;
     uint64_t nnz_cap = 0;
 };
@@ -416,7 +419,8 @@ int launch_exclusive_scan(const uint32_t *in, uint32_t *out, uint32_t n, uint32_
 // res->deadline_ns = now + limit_ms (or 0 when limit_ms is 0).
 int launch_set_deadline(DevResult *res, uint64_t limit_ms, cudaStream_t s);
 int launch_union_build(const BatchSrc *src, uint32_t G, uint32_t n_total, uint64_t *urp,
-                       uint32_t *ucol, uint32_t *graph_of, uint32_t *idmap, cudaStream_t s);
+                       uint32_t *ucol, uint32_t *graph_of, uint32_t *idmap, uint8_t *kmap,
+                       cudaStream_t s);
 int launch_graph_sums(const BatchSrc *src, uint32_t G, const unsigned long long *vcount,
                       const unsigned long long *vcks, unsigned long long *out_count,
                       unsigned long long *out_cks, cudaStream_t s);

@@ -70,19 +70,23 @@ __global__ void k_validate(uint32_t n, uint64_t nnz, const uint64_t *__restrict_
 // < k-1; each round, every queued vertex lowers the degree of its alive
 // neighbours and a neighbour whose degree falls from k-1 to k-2 joins the
 // next queue (exactly one thread sees that transition).
+// thr = k-1, or per vertex kmap[v] - 1 when a k map is given (batches of
+// graphs with different k).
 __global__ void k_precore_init(uint32_t n, const uint64_t *__restrict__ rp, uint32_t thr,
-                               uint8_t *alive, uint32_t *cdeg, uint32_t *fout, unsigned *fcount) {
+                               const uint8_t *__restrict__ kmap, uint8_t *alive, uint32_t *cdeg,
+                               uint32_t *fout, unsigned *fcount) {
     for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
         uint32_t d = (uint32_t)(rp[v + 1] - rp[v]);
         cdeg[v] = d;
-        bool keep = d >= thr;
+        bool keep = d >= (kmap ? kmap[v] - 1u : thr);
         alive[v] = keep ? 1 : 0;
         if (!keep) fout[atomicAdd(fcount, 1u)] = v;
     }
 }
 
 __global__ void k_precore_round(const uint64_t *__restrict__ rp, const uint32_t *__restrict__ col,
-                                uint32_t thr, const uint32_t *__restrict__ fin, uint32_t nin,
+                                uint32_t thr, const uint8_t *__restrict__ kmap,
+                                const uint32_t *__restrict__ fin, uint32_t nin,
                                 uint8_t *alive, uint32_t *cdeg, uint32_t *fout, unsigned *fcount) {
     const unsigned lane = lane_id();
     for (uint32_t i = warp_global(); i < nin; i += warps_total()) {
@@ -91,7 +95,7 @@ __global__ void k_precore_round(const uint64_t *__restrict__ rp, const uint32_t 
             uint32_t w = col[e];
             if (!alive[w]) continue;
             uint32_t old = atomicSub(&cdeg[w], 1u);
-            if (old == thr) {  // fell from k-1 to k-2
+            if (old == (kmap ? kmap[w] - 1u : thr)) {  // fell from k-1 to k-2
                 alive[w] = 0;
                 fout[atomicAdd(fcount, 1u)] = w;
             }
@@ -181,7 +185,8 @@ __device__ unsigned long long binom64(unsigned long long n, unsigned k, bool *ov
     return r;
 }
 
-__global__ void k_uf_check(uint32_t n, uint32_t k, const uint8_t *__restrict__ alive,
+__global__ void k_uf_check(uint32_t n, uint32_t k, const uint8_t *__restrict__ kmap,
+                           const uint8_t *__restrict__ alive,
                            const uint32_t *__restrict__ parent, const uint32_t *__restrict__ comp_n,
                            const unsigned long long *__restrict__ comp_sdeg, uint32_t *comp_flag,
                            uint32_t *comp_slot, unsigned long long *vcount, DevResult *res) {
@@ -190,7 +195,7 @@ __global__ void k_uf_check(uint32_t n, uint32_t k, const uint8_t *__restrict__ a
         unsigned long long nc = comp_n[v];
         if (comp_sdeg[v] != nc * (nc - 1)) continue;
         bool ovf = false;
-        unsigned long long c = binom64(nc, k, &ovf);
+        unsigned long long c = binom64(nc, kmap ? kmap[v] : k, &ovf);  // a component lies in one graph
         if (ovf) atomicOr(&res->status, DEV_ERR_OVERFLOW);
         add_count(&res->pre_count, &res->count_carry, c);
         if (vcount && c) atomicAdd(&vcount[v], c);  // attributed to the component's root
@@ -254,12 +259,13 @@ __device__ unsigned long long binom_small(unsigned long long n, unsigned k) {
     return ovf ? ~0ull : r;
 }
 
-__global__ void k_comp_emit(uint32_t k, const uint32_t *__restrict__ offs,
+__global__ void k_comp_emit(uint32_t kk, const uint8_t *__restrict__ kmap, const uint32_t *__restrict__ offs,
                             const uint32_t *__restrict__ sizes, const uint32_t *__restrict__ members,
                             uint32_t *ring, unsigned long long capacity, int wrap,
                             const uint32_t *__restrict__ croots, unsigned long long *vcks,
                             const uint32_t *__restrict__ idmap, DevResult *res) {
     uint32_t s = blockIdx.x;
+    const uint32_t k = kmap ? kmap[croots[s]] : kk;
     const uint32_t *m = members + offs[s];
     uint32_t nc = sizes[s];
     if (nc < k) return;
@@ -580,11 +586,12 @@ __global__ void k_outfill(uint32_t n, const uint64_t *__restrict__ rp, const uin
 // out-degree order by a counting sort: hist index = max_outdeg - d+.
 __global__ void k_root_hist(uint32_t n, uint32_t k, const uint8_t *__restrict__ alive,
                             const uint32_t *__restrict__ outdeg, uint32_t max_outdeg, uint32_t *hist,
-                            const uint8_t *__restrict__ mask, DevResult *res) {
+                            const uint8_t *__restrict__ mask, const uint8_t *__restrict__ kmap,
+                            DevResult *res) {
     uint32_t cnt = 0;
     for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
         uint32_t d = outdeg[v];
-        if (alive[v] && d + 1 >= k && (!mask || mask[v])) {
+        if (alive[v] && d + 1 >= (kmap ? kmap[v] : k) && (!mask || mask[v])) {
             atomicAdd(&hist[max_outdeg - d], 1u);
             cnt++;
         }
@@ -596,10 +603,11 @@ __global__ void k_root_hist(uint32_t n, uint32_t k, const uint8_t *__restrict__ 
 __global__ void k_root_scatter(uint32_t n, uint32_t k, const uint8_t *__restrict__ alive,
                                const uint32_t *__restrict__ outdeg, uint32_t max_outdeg,
                                const uint32_t *__restrict__ offs, uint32_t *fill,
-                               const uint8_t *__restrict__ mask, uint32_t *roots) {
+                               const uint8_t *__restrict__ mask, const uint8_t *__restrict__ kmap,
+                               uint32_t *roots) {
     for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
         uint32_t d = outdeg[v];
-        if (alive[v] && d + 1 >= k && (!mask || mask[v])) {
+        if (alive[v] && d + 1 >= (kmap ? kmap[v] : k) && (!mask || mask[v])) {
             uint32_t h = max_outdeg - d;
             roots[offs[h] + atomicAdd(&fill[h], 1u)] = v;
         }
@@ -686,12 +694,13 @@ __global__ void k_scan_add(uint32_t *out, uint32_t n, const uint32_t *__restrict
 // Disjoint union of a batch of graphs: block b copies graph b's rows and
 // columns with its vertex offset voff[b] and edge offset eoff[b].
 __global__ void k_union_build(const BatchSrc *__restrict__ src, uint32_t n_total, uint64_t *urp,
-                              uint32_t *ucol, uint32_t *graph_of, uint32_t *idmap) {
+                              uint32_t *ucol, uint32_t *graph_of, uint32_t *idmap, uint8_t *kmap) {
     const BatchSrc b = src[blockIdx.x];
     for (uint32_t v = threadIdx.x; v < b.n; v += blockDim.x) {
         urp[b.voff + v] = b.rp[v] + b.eoff;
         graph_of[b.voff + v] = blockIdx.x;
         idmap[b.voff + v] = v;
+        kmap[b.voff + v] = (uint8_t)b.k;
     }
     for (uint64_t e = threadIdx.x; e < b.nnz; e += blockDim.x) ucol[b.eoff + e] = b.col[e] + b.voff;
     if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) urp[n_total] = b.eoff + b.nnz;
@@ -723,9 +732,10 @@ __global__ void k_graph_sums(const BatchSrc *__restrict__ src, const unsigned lo
 }
 
 int launch_union_build(const BatchSrc *src, uint32_t G, uint32_t n_total, uint64_t *urp,
-                       uint32_t *ucol, uint32_t *graph_of, uint32_t *idmap, cudaStream_t s) {
+                       uint32_t *ucol, uint32_t *graph_of, uint32_t *idmap, uint8_t *kmap,
+                       cudaStream_t s) {
     if (G == 0) return 0;
-    k_union_build<<<G, 256, 0, s>>>(src, n_total, urp, ucol, graph_of, idmap);
+    k_union_build<<<G, 256, 0, s>>>(src, n_total, urp, ucol, graph_of, idmap, kmap);
     return 1;
 }
 
@@ -770,16 +780,17 @@ int launch_validate(const kcl_graph *g, DevResult *res, cudaStream_t s) {
 
 int launch_precore_init(const kcl_graph *g, uint32_t k, Workspace &w, cudaStream_t s) {
     int grid = grid_for(g->n, kBlock, g->num_sms);
-    k_precore_init<<<grid, kBlock, 0, s>>>(g->n, g->rp, k - 1, w.alive, w.cdeg, w.frontier_a,
-                                           &w.res->frontier);
+    // a threshold of 0 (k = 1: Pre-Core switched off) keeps every vertex, whatever the k map says
+    k_precore_init<<<grid, kBlock, 0, s>>>(g->n, g->rp, k - 1, k > 1 ? w.kmap : nullptr, w.alive,
+                                           w.cdeg, w.frontier_a, &w.res->frontier);
     return 1;
 }
 
 int launch_precore_round(const kcl_graph *g, uint32_t k, const uint32_t *fin, uint32_t nin,
                          uint32_t *fout, Workspace &w, cudaStream_t s) {
     int grid = grid_for((uint64_t)nin * 32, kBlock, g->num_sms, 32);
-    k_precore_round<<<grid, kBlock, 0, s>>>(g->rp, g->col, k - 1, fin, nin, w.alive, w.cdeg, fout,
-                                            &w.res->frontier);
+    k_precore_round<<<grid, kBlock, 0, s>>>(g->rp, g->col, k - 1, k > 1 ? w.kmap : nullptr, fin, nin,
+                                            w.alive, w.cdeg, fout, &w.res->frontier);
     return 1;
 }
 
@@ -789,7 +800,7 @@ int launch_prelist(const kcl_graph *g, uint32_t k, Workspace &w, int listing, cu
     k_uf_init<<<grid, kBlock, 0, s>>>(g->n, w.parent, w.comp_n, w.comp_sdeg, w.comp_flag);
     k_uf_hook<<<wgrid, kBlock, 0, s>>>(g->n, g->rp, g->col, w.alive, w.parent);
     k_uf_stats<<<grid, kBlock, 0, s>>>(g->n, w.alive, w.parent, w.cdeg, w.comp_n, w.comp_sdeg);
-    k_uf_check<<<grid, kBlock, 0, s>>>(g->n, k, w.alive, w.parent, w.comp_n, w.comp_sdeg,
+    k_uf_check<<<grid, kBlock, 0, s>>>(g->n, k, w.kmap, w.alive, w.parent, w.comp_n, w.comp_sdeg,
                                        w.comp_flag, listing ? w.comp_slot : nullptr, w.vcount_pre,
                                        w.res);
     k_uf_remove<<<grid, kBlock, 0, s>>>(g->n, w.alive, w.parent, w.comp_flag);
@@ -810,7 +821,7 @@ int launch_prelist_emit(const kcl_graph *g, uint32_t k, Workspace &w, uint32_t n
                                           offs, fill, w.members);
     k_comp_sort<<<n_comps, 256, 0, s>>>(offs, sizes, w.members);
     const bool to_ring = ring && ring->ids && ring->capacity;
-    k_comp_emit<<<n_comps, 256, 0, s>>>(k, offs, sizes, w.members, to_ring ? ring->ids : nullptr,
+    k_comp_emit<<<n_comps, 256, 0, s>>>(k, w.kmap, offs, sizes, w.members, to_ring ? ring->ids : nullptr,
                                         to_ring ? ring->capacity : 0, to_ring ? ring->wrap : 0,
                                         croots, w.vcks_pre, w.idmap, w.res);
     return l + 3;
@@ -908,10 +919,11 @@ int launch_roots(const kcl_graph *g, uint32_t k, Workspace &w, uint32_t max_outd
     uint32_t *limits = w.hist + 3 * (H + 1);
     cudaMemsetAsync(w.hist, 0, 3 * (H + 1) * sizeof(uint32_t), s);
     cudaMemcpyAsync(limits, class_limits, n_classes * sizeof(uint32_t), cudaMemcpyHostToDevice, s);
-    k_root_hist<<<grid, kBlock, 0, s>>>(g->n, k, w.alive, w.outdeg, max_outdeg, hist, w.root_mask, w.res);
+    k_root_hist<<<grid, kBlock, 0, s>>>(g->n, k, w.alive, w.outdeg, max_outdeg, hist, w.root_mask,
+                                        w.kmap, w.res);
     int l = 1 + launch_exclusive_scan(hist, offs, H + 1, w.scan_tmp, s);
     k_root_scatter<<<grid, kBlock, 0, s>>>(g->n, k, w.alive, w.outdeg, max_outdeg, offs, fill,
-                                           w.root_mask, w.roots);
+                                           w.root_mask, w.kmap, w.roots);
     // class bounds into the tail of hist; n_roots = offs[H]
     uint32_t *cb = w.hist + 3 * (H + 1) + 64;
     k_class_bounds<<<1, 64, 0, s>>>(offs, max_outdeg, limits, n_classes, 0, cb);

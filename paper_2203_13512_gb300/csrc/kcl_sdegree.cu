@@ -43,6 +43,7 @@ struct Emit {
     const uint32_t *idmap;         // listing: vertex -> output id, or null (identity)
     unsigned long long *slots;     // CTA form: work-splitting slots (one per CTA)
     uint32_t split;                // CTA form: help a root with >= split children left (0 = off)
+    const uint8_t *kmap;           // batches: k of each root's graph (null: the launch's k)
 };
 
 // lower_bound of x in a sorted list
@@ -1052,7 +1053,7 @@ __host__ __device__ inline size_t cta_arena_words(uint32_t D) {
 }
 
 template <bool LIST>
-__global__ void __launch_bounds__(512) k_sdegree_cta(uint32_t k, uint32_t D, const uint32_t *__restrict__ optr,
+__global__ void __launch_bounds__(512) k_sdegree_cta(uint32_t kmax, uint32_t D, const uint32_t *__restrict__ optr,
                                                     const uint32_t *__restrict__ oadj,
                                                     const uint32_t *__restrict__ key,
                                                     const uint32_t *__restrict__ roots, uint32_t begin,
@@ -1096,7 +1097,7 @@ __global__ void __launch_bounds__(512) k_sdegree_cta(uint32_t k, uint32_t D, con
         if (idx >= end - begin) {
             queue_done = true;
             // no root left: help the root with the most children left
-            if (!em.split || k == 3 || late) break;
+            if (!em.split || kmax == 3 || late) break;
             if (warp == 0) {
                 uint32_t pos = 0;
                 const int j = split_pick(em.slots, gridDim.x, blockIdx.x, em.split, &pos);
@@ -1109,6 +1110,7 @@ __global__ void __launch_bounds__(512) k_sdegree_cta(uint32_t k, uint32_t D, con
         }
         unsigned long long *slot = helping >= 0 ? em.slots + helping : my_slot;
         const uint32_t u = roots[begin + idx];
+        const uint32_t k = em.kmap ? (uint32_t)em.kmap[u] : kmax;
         const uint32_t base = optr[u], d = optr[u + 1] - base;
         const unsigned long long before = cnt;
         const unsigned long long before_cks = cks;
@@ -1358,7 +1360,7 @@ __global__ void __launch_bounds__(512) k_sdegree_cta(uint32_t k, uint32_t D, con
 }
 
 template <bool LIST, bool GLOBAL, bool LOCAL>
-__global__ void __launch_bounds__(128) k_sdegree(uint32_t k, uint32_t D, const uint32_t *__restrict__ optr,
+__global__ void __launch_bounds__(128) k_sdegree(uint32_t kmax, uint32_t D, const uint32_t *__restrict__ optr,
                                                 const uint32_t *__restrict__ oadj,
                                                 const uint32_t *__restrict__ key,
                                                 const uint32_t *__restrict__ roots, uint32_t begin,
@@ -1380,6 +1382,7 @@ __global__ void __launch_bounds__(128) k_sdegree(uint32_t k, uint32_t D, const u
         idx = __shfl_sync(kFull, idx, 0);
         if (idx >= end - begin) break;
         uint32_t u = roots[begin + idx];
+        const uint32_t k = em.kmap ? (uint32_t)em.kmap[u] : kmax;
         unsigned long long before = cnt;
         const unsigned long long before_cks = cks;
         if (LOCAL) sdegree_root_local<LIST>(u, k, D, optr, oadj, key, S, em, res, gallop, bitmap, cnt, cks);
@@ -1507,7 +1510,7 @@ size_t sdegree_arena_words(uint32_t k, int num_sms, uint32_t max_outdeg) {
 
 int launch_sdegree(const kcl_graph *g, uint32_t k, Workspace &w, const uint32_t *class_begin,
                    int n_classes, const ListArgs &la, cudaStream_t s) {
-    Emit em{la.ring, la.capacity, la.wrap, la.per_root_cks, la.idmap, w.slots, 0u};
+    Emit em{la.ring, la.capacity, la.wrap, la.per_root_cks, la.idmap, w.slots, 0u, w.kmap};
     int launches = 0;
     cudaMemsetAsync(w.queue, 0, 64 * sizeof(unsigned), s);
     for (int c = 0; c < n_classes; c++) {
