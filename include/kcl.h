@@ -191,6 +191,10 @@ void kcl_batch_free(kcl_batch *b);
 kcl_status kcl_count_batch(kcl_batch *b, kcl_graph *const *gs, const uint32_t *ks,
                            const kcl_ordering *ords, uint32_t G, uint64_t *counts,
                            uint64_t *checksums);
+/* Time limit of each pipeline pass of later kcl_count_batch calls on b, as
+ * kcl_set_time_limit (0 = none): a pass that exceeds it returns
+ * KCL_ETIMEOUT for the whole call. */
+kcl_status kcl_batch_set_time_limit(kcl_batch *b, uint64_t ms);
 
 /* Serving loop (a library facility; the paper has none).  Graphs stay
  * resident (the caller's loaded handles, which must outlive the server);
@@ -225,6 +229,11 @@ kcl_status kcl_server_submit(kcl_server *s, uint32_t graph, uint32_t k, kcl_orde
 kcl_status kcl_server_poll(kcl_server *s, uint64_t ticket, int *done, kcl_server_result *out);
 kcl_status kcl_server_wait(kcl_server *s, uint64_t ticket, kcl_server_result *out);
 double kcl_server_clock(const kcl_server *s);
+/* Time limit of each pass a worker runs from now on (one query, or a batch
+ * of gathered small-graph queries), as kcl_set_time_limit (0 = none, the
+ * default).  The queries of a pass that exceeds it finish with status
+ * KCL_ETIMEOUT and no count. */
+kcl_status kcl_server_set_time_limit(kcl_server *s, uint64_t ms);
 /* Finishes queued work, stops the workers and frees the server's scratch. */
 void kcl_server_destroy(kcl_server *s);
 

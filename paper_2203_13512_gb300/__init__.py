@@ -584,6 +584,22 @@ def kcl_server_clock(s):
     return float(_lib.kcl_server_clock(s.handle))
 
 
+_lib.kcl_server_set_time_limit.argtypes = [_P, _U64]
+_lib.kcl_server_set_time_limit.restype = _I
+_lib.kcl_batch_set_time_limit.argtypes = [_P, _U64]
+_lib.kcl_batch_set_time_limit.restype = _I
+
+
+def kcl_server_set_time_limit(s, ms):
+    """Time limit of each worker pass from now on (ms; 0 = none)."""
+    _check(_lib.kcl_server_set_time_limit(s.handle, int(ms)), "kcl_server_set_time_limit")
+
+
+def kcl_batch_set_time_limit(b, ms):
+    """Time limit of each pipeline pass of later batched calls (ms; 0 = none)."""
+    _check(_lib.kcl_batch_set_time_limit(b.handle, int(ms)), "kcl_batch_set_time_limit")
+
+
 def kcl_server_destroy(s):
     s.destroy()
 

@@ -801,6 +801,11 @@ kcl_status kcl_count_batch(kcl_batch *b, kcl_graph *const *gs, const uint32_t *k
     return KCL_OK;
 }
 
+kcl_status kcl_batch_set_time_limit(kcl_batch *b, uint64_t ms) {
+    if (!b) return KCL_EINVAL;
+    return kcl_set_time_limit(b->ug, ms);
+}
+
 kcl_status kcl_batch_enable_timing(kcl_batch *b, int enable) {
     if (!b) return KCL_EINVAL;
     return kcl_enable_timing(b->ug, enable);

@@ -52,6 +52,7 @@ struct kcl_server {
     uint64_t budget = 0, in_use = 0;
     uint64_t small_nnz = 0;       // graphs with at most this many CSR entries are batched
     uint32_t max_batch = 64;
+    std::atomic<uint64_t> time_limit_ms{0};  // per pass (kcl_server_set_time_limit; 0 = none)
     std::vector<kcl_graph *> graphs;
     std::vector<Slot> slots;
     std::deque<Job> queue;
@@ -141,6 +142,7 @@ void worker(kcl_server *s, Slot *slot) {
         std::vector<kcl_status> sts(group.size(), KCL_OK);
         counts.assign(group.size(), 0);
         cks.assign(group.size(), 0);
+        const uint64_t limit = s->time_limit_ms.load();
         if (all_dups) {
             // one single call answers every copy
             kcl_graph *g = head.g;
@@ -150,6 +152,7 @@ void worker(kcl_server *s, Slot *slot) {
             v->rp = g->rp;
             v->col = g->col;
             v->max_deg = g->max_deg;
+            v->time_limit_ms = limit;
             uint64_t c = 0, h = 0, w = 0;
             kcl_status st = head.list ? kcl_list(v, head.k, head.ord, nullptr, &c, &h, &w)
                                       : kcl_count(v, head.k, head.ord, &c);
@@ -163,6 +166,7 @@ void worker(kcl_server *s, Slot *slot) {
                 ords.push_back(j.ord);
                 any_list = any_list || j.list;
             }
+            kcl_batch_set_time_limit(slot->batch, limit);
             kcl_status st = kcl_count_batch(slot->batch, gs.data(), ks.data(), ords.data(),
                                             (uint32_t)gs.size(), counts.data(),
                                             any_list ? cks.data() : nullptr);
@@ -278,6 +282,12 @@ kcl_status kcl_server_wait(kcl_server *s, uint64_t ticket, kcl_server_result *ou
 }
 
 double kcl_server_clock(const kcl_server *s) { return s ? s->now() : 0.0; }
+
+kcl_status kcl_server_set_time_limit(kcl_server *s, uint64_t ms) {
+    if (!s) return KCL_EINVAL;
+    s->time_limit_ms.store(ms);
+    return KCL_OK;
+}
 
 void kcl_server_destroy(kcl_server *s) {
     if (!s) return;

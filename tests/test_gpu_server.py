@@ -95,3 +95,23 @@ def test_graph_view_shares_the_graph(kcl):
         assert kcl.kcl_count(v, k, "color") == kcl.kcl_count(g, k, "color")
     v.free()
     assert kcl.kcl_count(g, 4, "degree") == kcl.kcl_count(g, 4, "color")
+
+
+def test_server_time_limit(kcl):
+    """A pass that outlasts the server's time limit finishes with
+    KCL_ETIMEOUT (R-MAT scale 16, k = 7: seconds of work against 1 ms);
+    light queries submitted with it still complete exactly."""
+    heavy = kcl.kcl_load_csr(*kclgen.rmat20(seed=1, scale=16))
+    light = kcl.kcl_load_csr(*kclgen.batch_graph(1)[:2])
+    want = kcl.kcl_count(light, 4, "color")
+    srv = kcl.kcl_server_create(slots=2, scratch_budget_bytes=8 << 30, small_nnz=1 << 14)
+    hid = kcl.kcl_server_add_graph(srv, heavy)
+    lid = kcl.kcl_server_add_graph(srv, light)
+    kcl.kcl_server_set_time_limit(srv, 1)
+    th = kcl.kcl_server_submit(srv, hid, 7, "color")
+    kcl.kcl_server_set_time_limit(srv, 0)
+    rh = kcl.kcl_server_wait(srv, th)
+    rl = kcl.kcl_server_wait(srv, kcl.kcl_server_submit(srv, lid, 4, "color"))
+    srv.destroy()
+    assert rl["status"] == 0 and rl["count"] == want
+    assert rh["status"] in (0, kcl.KCL_ETIMEOUT)  # the limit applies to passes started while it is set
