@@ -108,10 +108,9 @@ def test_server_time_limit(kcl):
     hid = kcl.kcl_server_add_graph(srv, heavy)
     lid = kcl.kcl_server_add_graph(srv, light)
     kcl.kcl_server_set_time_limit(srv, 1)
-    th = kcl.kcl_server_submit(srv, hid, 7, "color")
+    rh = kcl.kcl_server_wait(srv, kcl.kcl_server_submit(srv, hid, 7, "color"))
+    assert rh["status"] == kcl.KCL_ETIMEOUT
     kcl.kcl_server_set_time_limit(srv, 0)
-    rh = kcl.kcl_server_wait(srv, th)
     rl = kcl.kcl_server_wait(srv, kcl.kcl_server_submit(srv, lid, 4, "color"))
     srv.destroy()
     assert rl["status"] == 0 and rl["count"] == want
-    assert rh["status"] in (0, kcl.KCL_ETIMEOUT)  # the limit applies to passes started while it is set
