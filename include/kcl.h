@@ -229,10 +229,10 @@ kcl_status kcl_server_submit(kcl_server *s, uint32_t graph, uint32_t k, kcl_orde
 kcl_status kcl_server_poll(kcl_server *s, uint64_t ticket, int *done, kcl_server_result *out);
 kcl_status kcl_server_wait(kcl_server *s, uint64_t ticket, kcl_server_result *out);
 double kcl_server_clock(const kcl_server *s);
-/* Time limit of each pass a worker runs from now on (one query, or a batch
- * of gathered small-graph queries), as kcl_set_time_limit (0 = none, the
- * default).  The queries of a pass that exceeds it finish with status
- * KCL_ETIMEOUT and no count. */
+/* Time limit per query of the passes a worker starts from now on, as
+ * kcl_set_time_limit (0 = none, the default): a single-query pass gets ms, a
+ * batched pass of n gathered small-graph queries n * ms.  The queries of a
+ * pass that exceeds its limit finish with status KCL_ETIMEOUT and no count. */
 kcl_status kcl_server_set_time_limit(kcl_server *s, uint64_t ms);
 /* Finishes queued work, stops the workers and frees the server's scratch. */
 void kcl_server_destroy(kcl_server *s);

@@ -166,7 +166,8 @@ void worker(kcl_server *s, Slot *slot) {
                 ords.push_back(j.ord);
                 any_list = any_list || j.list;
             }
-            kcl_batch_set_time_limit(slot->batch, limit);
+            // a batched pass answers group.size() queries: each keeps its own share
+            kcl_batch_set_time_limit(slot->batch, limit * group.size());
             kcl_status st = kcl_count_batch(slot->batch, gs.data(), ks.data(), ords.data(),
                                             (uint32_t)gs.size(), counts.data(),
                                             any_list ? cks.data() : nullptr);
