@@ -232,9 +232,11 @@ bool run_peel_coop(kcl_graph *g, StageTimer &T) {
         (void)cudaGetLastError();
         return false;
     }
-    // the remaining-vertex lists use the root-histogram scratch (3n + 1024
-    // words), which is free until the roots are sorted after the peel
-    int l = launch_peel_coop(g, w, w.peel, w.hist, w.hist + g->n, s);
+    // the remaining-vertex lists (n words each) and the big-row lists (n / 2
+    // each) use the root-histogram scratch (3n + 1024 words), which is free
+    // until the roots are sorted after the peel
+    const size_t n = g->n;
+    int l = launch_peel_coop(g, w, w.peel, w.hist, w.hist + n, w.hist + 2 * n, w.hist + 2 * n + n / 2 + 1, s);
     if (l < 0) {
         (void)cudaGetLastError();
         return false;

@@ -46,10 +46,10 @@ struct DevResult {
 // levels).  All zero at launch except minv, all ones.
 struct PeelCtl {
     unsigned bar_count, bar_gen, error, remaining;
-    unsigned fcnt[3];
+    unsigned fcnt[3];   // frontier sizes (vertices up to the big-degree threshold)
     unsigned rcnt[2];
     unsigned minv[2];
-    unsigned pad[3];
+    unsigned bcnt[3];   // big-vertex frontier sizes (rotating like fcnt)
 };
 
 // One graph of a batch: its device CSR and its place in the disjoint union.
@@ -407,9 +407,11 @@ int launch_peel_update(const kcl_graph *g, Workspace &w, const uint32_t *fin, ui
 int launch_peel_min(const kcl_graph *g, Workspace &w, cudaStream_t s);
 // Whole degeneracy peel in one cooperative launch; -1 if it cannot launch.
 // rl0/rl1: two n-entry arrays for the compacted remaining-vertex lists (or
-// both null: every threshold rise scans all n vertices).
+// both null: every threshold rise scans all n vertices); bl0/bl1: two
+// n/2-entry arrays for the frontier's big-degree vertices, whose rows the
+// whole grid walks together (or null: every frontier vertex takes one warp).
 int launch_peel_coop(const kcl_graph *g, Workspace &w, PeelCtl *ctl, uint32_t *rl0, uint32_t *rl1,
-                     cudaStream_t s);
+                     uint32_t *bl0, uint32_t *bl1, cudaStream_t s);
 int launch_orient(const kcl_graph *g, uint32_t k, Workspace &w, cudaStream_t s);
 int launch_roots(const kcl_graph *g, uint32_t k, Workspace &w, uint32_t max_outdeg,
                  uint32_t *class_begin, const uint32_t *class_limits, int n_classes,

@@ -384,41 +384,55 @@ __global__ void k_peel_update(const uint64_t *__restrict__ rp, const uint32_t *_
 // KCL_ETIMEOUT.
 constexpr unsigned long long kSpinLimit = 1ull << 25;
 
+__device__ __forceinline__ unsigned ld_acquire(const unsigned *p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ unsigned atom_add_acq_rel(unsigned *p, unsigned x) {
+    unsigned old;
+    asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(x) : "memory");
+    return old;
+}
+
+// Generation barrier: thread 0 of each block arrives with an acquire-release
+// add (publishing the block's writes, which __syncthreads has ordered before
+// it); the last arrival clears the count and bumps the generation with a
+// release, and the others poll the generation with acquire loads.
 __device__ bool grid_barrier(PeelCtl *c, unsigned nblocks) {
     __shared__ int ok_s;
     __syncthreads();
     if (threadIdx.x == 0) {
-        volatile unsigned *gen = &c->bar_gen;
-        volatile unsigned *err = &c->error;
-        unsigned g = *gen;
-        __threadfence();
-        unsigned arrived = atomicAdd(&c->bar_count, 1u);
+        const unsigned g = ld_acquire(&c->bar_gen);
+        const unsigned arrived = atom_add_acq_rel(&c->bar_count, 1u);
         int ok = 1;
         if (arrived == nblocks - 1) {
             atomicExch(&c->bar_count, 0u);
-            __threadfence();
-            atomicAdd(&c->bar_gen, 1u);
+            atom_add_acq_rel(&c->bar_gen, 1u);
         } else {
             unsigned long long spins = 0;
-            while (*gen == g) {
-                if (*err) { ok = 0; break; }
+            while (ld_acquire(&c->bar_gen) == g) {
+                if (ld_acquire(&c->error)) { ok = 0; break; }
                 if (++spins > kSpinLimit) { atomicExch(&c->error, 1u); ok = 0; break; }
-                __nanosleep(32);
             }
         }
-        __threadfence();
-        ok_s = ok && *err == 0;
+        ok_s = ok && ld_acquire(&c->error) == 0;
     }
     __syncthreads();
     return ok_s != 0;
 }
 
+// A frontier vertex whose row is longer than `big` goes to a separate list
+// (bl0/bl1 by round parity) and its row is walked by every thread of the grid
+// instead of one warp, so a hub does not stretch its round.
 __global__ void __launch_bounds__(1024) k_peel_coop(uint32_t n, const uint64_t *__restrict__ rp,
                                                     const uint32_t *__restrict__ col,
                                                     const uint8_t *__restrict__ alive,
                                                     const uint32_t *__restrict__ cdeg, uint32_t *pdeg,
                                                     uint32_t *key, uint32_t *fa, uint32_t *fb,
-                                                    uint32_t *rl0, uint32_t *rl1, PeelCtl *c) {
+                                                    uint32_t *rl0, uint32_t *rl1, uint32_t *bl0,
+                                                    uint32_t *bl1, uint64_t big, PeelCtl *c) {
     const unsigned nblocks = gridDim.x;
     const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
     const uint32_t nth = gridDim.x * blockDim.x;
@@ -454,8 +468,11 @@ __global__ void __launch_bounds__(1024) k_peel_coop(uint32_t n, const uint64_t *
         const uint32_t fi = round % 3u;
         uint32_t *fin = (round & 1u) ? fb : fa;
         uint32_t *fout = (round & 1u) ? fa : fb;
+        uint32_t *bin = (round & 1u) ? bl1 : bl0;
+        uint32_t *bout = (round & 1u) ? bl0 : bl1;
         uint32_t nin = vc->fcnt[fi];
-        if (nin == 0) {
+        uint32_t nbig = vc->bcnt[fi];
+        if (nin + nbig == 0) {
             // t rises to the minimum remaining degree
             const uint32_t lp = level & 1u;
             const uint32_t *rl = lp ? rl1 : rl0;
@@ -479,13 +496,15 @@ __global__ void __launch_bounds__(1024) k_peel_coop(uint32_t n, const uint64_t *
             // select the frontier; compact the rest into the other list
             for (uint32_t i0 = tid - lane; i0 < nr; i0 += nth) {
                 const uint32_t i = i0 + lane;
-                bool sel = false, keep = false;
+                bool sel = false, keep = false, sbig = false;
                 uint32_t v = 0;
                 if (i < nr) {
                     v = lists ? __ldcg(&rl[i]) : i;
                     if ((lists || alive[v]) && __ldcg(&key[v]) == 0xFFFFFFFFu) {
                         sel = __ldcg(&pdeg[v]) <= t;
                         keep = !sel;
+                        sbig = sel && bl0 && rp[v + 1] - rp[v] > big;
+                        sel = sel && !sbig;
                     }
                 }
                 const unsigned ms = __ballot_sync(0xffffffffu, sel);
@@ -495,6 +514,10 @@ __global__ void __launch_bounds__(1024) k_peel_coop(uint32_t n, const uint64_t *
                 if (sel) {
                     key[v] = round;
                     fin[bs + __popc(ms & ((1u << lane) - 1u))] = v;
+                }
+                if (sbig) {  // rare: one atomic each
+                    key[v] = round;
+                    bin[atomicAdd(&c->bcnt[fi], 1u)] = v;
                 }
                 if (lists) {
                     const unsigned mk = __ballot_sync(0xffffffffu, keep);
@@ -507,26 +530,38 @@ __global__ void __launch_bounds__(1024) k_peel_coop(uint32_t n, const uint64_t *
             level++;
             if (!grid_barrier(c, nblocks)) return;
             nin = vc->fcnt[fi];
-            if (nin == 0) {  // cannot happen while vertices remain
+            nbig = vc->bcnt[fi];
+            if (nin + nbig == 0) {  // cannot happen while vertices remain
                 if (tid == 0) atomicExch(&c->error, 2u);
                 return;
             }
         }
-        if (tid == 0) c->fcnt[(round + 2u) % 3u] = 0;  // every block read it two barriers ago
+        if (tid == 0) {  // every block read these two barriers ago
+            c->fcnt[(round + 2u) % 3u] = 0;
+            c->bcnt[(round + 2u) % 3u] = 0;
+        }
         // remove this round's vertices: lower the degrees of their remaining
         // neighbours; a neighbour reaching <= t joins the next round
         uint32_t *fnext_cnt = &c->fcnt[(round + 1u) % 3u];
+        uint32_t *bnext_cnt = &c->bcnt[(round + 1u) % 3u];
+        auto relax = [&](uint32_t w) {
+            if (!alive[w] || __ldcg(&key[w]) != 0xFFFFFFFFu) return;
+            const uint32_t nd = atomicSub(&pdeg[w], 1u) - 1u;
+            if (nd <= t && atomicCAS(&key[w], 0xFFFFFFFFu, round + 1) == 0xFFFFFFFFu) {
+                if (bl0 && rp[w + 1] - rp[w] > big) bout[atomicAdd(bnext_cnt, 1u)] = w;
+                else fout[atomicAdd(fnext_cnt, 1u)] = w;
+            }
+        };
+        for (uint32_t b = 0; b < nbig; b++) {  // big rows: the whole grid, one edge per thread
+            const uint32_t v = __ldcg(&bin[b]);
+            for (uint64_t e = rp[v] + tid; e < rp[v + 1]; e += nth) relax(col[e]);
+        }
         for (uint32_t i = tid >> 5; i < nin; i += nth >> 5) {
             const uint32_t v = __ldcg(&fin[i]);
-            for (uint64_t e = rp[v] + lane; e < rp[v + 1]; e += 32) {
-                const uint32_t w = col[e];
-                if (!alive[w] || __ldcg(&key[w]) != 0xFFFFFFFFu) continue;
-                const uint32_t nd = atomicSub(&pdeg[w], 1u) - 1u;
-                if (nd <= t && atomicCAS(&key[w], 0xFFFFFFFFu, round + 1) == 0xFFFFFFFFu)
-                    fout[atomicAdd(fnext_cnt, 1u)] = w;
-            }
+            for (uint64_t e = rp[v] + lane; e < rp[v + 1]; e += 32) relax(col[e]);
         }
-        remaining -= nin < remaining ? nin : remaining;
+        const uint32_t gone = nin + nbig;
+        remaining -= gone < remaining ? gone : remaining;
         round++;
         if (!grid_barrier(c, nblocks)) return;
     }
@@ -883,7 +918,7 @@ int peel_blocks(int num_sms, uint32_t n) {
 }
 
 int launch_peel_coop(const kcl_graph *g, Workspace &w, PeelCtl *ctl, uint32_t *rl0, uint32_t *rl1,
-                     cudaStream_t s) {
+                     uint32_t *bl0, uint32_t *bl1, cudaStream_t s) {
     int blocks = peel_blocks(g->num_sms, g->n);
     if (blocks <= 0) return -1;
     uint32_t n = g->n;
@@ -892,8 +927,12 @@ int launch_peel_coop(const kcl_graph *g, Workspace &w, PeelCtl *ctl, uint32_t *r
     const uint8_t *alive = w.alive;
     const uint32_t *cdeg = w.cdeg;
     uint32_t *pdeg = w.peel_deg, *key = w.key, *fa = w.frontier_a, *fb = w.frontier_b;
+    // big rows: longer than 2048 and than 4x the mean degree, so there are at
+    // most nnz / big <= n / 4 of them (each list holds n / 2)
+    const uint64_t mean = n ? (g->nnz + n - 1) / n : 0;
+    uint64_t big = 4 * mean > 2048 ? 4 * mean : 2048;
     void *args[] = {&n, (void *)&rp, (void *)&col, (void *)&alive, (void *)&cdeg, &pdeg, &key, &fa,
-                    &fb, &rl0, &rl1, &ctl};
+                    &fb, &rl0, &rl1, &bl0, &bl1, &big, &ctl};
     if (cudaLaunchCooperativeKernel((const void *)k_peel_coop, blocks, kPeelThreads, args, 0, s) !=
         cudaSuccess)
         return -1;
@@ -1013,8 +1052,10 @@ extern "C" kcl_status kcl_degeneracy_order_noalloc(uint32_t n, const uint64_t *r
     const uint32_t *deg = degree;
     uint32_t *key = round_out;
     uint32_t *rl0 = nullptr, *rl1 = nullptr;  // no room for remaining lists: full scans
+    uint32_t *bl0 = nullptr, *bl1 = nullptr;  // nor for big-row lists: a warp per frontier vertex
+    uint64_t big = ~0ull;
     void *args[] = {&nn, (void *)&rp, (void *)&c, (void *)&al, (void *)&deg, &pdeg, &key, &fa, &fb,
-                    &rl0, &rl1, &ctl};
+                    &rl0, &rl1, &bl0, &bl1, &big, &ctl};
     if (cudaLaunchCooperativeKernel((const void *)kcl::k_peel_coop, blocks, kcl::kPeelThreads, args, 0, s) !=
         cudaSuccess) {
         (void)cudaGetLastError();
