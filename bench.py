@@ -484,8 +484,11 @@ KERNEL_NAMES = {
 # capture of the same workload, keyed (k, ordering, mode, class); the source
 # names the summary under profiles/.  An entry is removed when its kernel
 # changes, until a new capture exists.
-_DRAM = "profiles/dram_listing_kernels_rmat20.md"
-TRAFFIC = {}
+_DRAM = "profiles/k_bitcol_cta_rmat20.md"
+TRAFFIC = {
+    (5, "color", "count", 4): (30.727e6 + 0.048e6, _DRAM),
+    (4, "color", "list", 4): (3.102e9 + 192.306e9, _DRAM),
+}
 
 
 def class_work(entry, lo, hi, field="work_by_outdeg"):
