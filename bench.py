@@ -284,6 +284,27 @@ def run_ours(args, rank, world):
         res["c2_k6"] = {"orderings": k6, "orderings_agree": len({v["count"] for v in k6.values()}) == 1,
                         "k_cliques_per_s": tot / (sum(v["ms"] for v in k6.values()) / 1e3)}
     g.free()
+    if not args.no_forms:
+        # bounded samples of the batched and served forms (their own
+        # --form lines run them at full size)
+        bt = batch_form(args.summary_batch_graphs, quiet=True)
+        res["batched"] = {"graphs": bt["config"]["graphs"],
+                          "batched_graphs_per_s": bt["value"],
+                          "per_graph_graphs_per_s": bt["per_graph_value"],
+                          "speedup": bt["speedup"], "bit_exact": bt["bit_exact"],
+                          "sample": "graphs 0..%d of the batched workload, both orderings, "
+                                    "count + checksum" % (bt["config"]["graphs"] - 1)}
+        sv = serve_form(args.summary_serve_queries, [10000.0], args.serve_limit_ms,
+                        rmat_ids=range(1, 9), batch_ids=range(33, 57), rmat_scale=lambda i: 16,
+                        quiet=True)
+        r = sv["rates"]["10000.0"]
+        res["served"] = {"queries": sv["config"]["queries"], "rate_per_s": 10000.0,
+                         "time_limit_ms": args.serve_limit_ms,
+                         "served": r["served"], "fifo": r["fifo"],
+                         "results_compared_equal": sv["results_compared_equal"],
+                         "bit_exact": sv["bit_exact"],
+                         "sample": "8 R-MAT scale-16 graphs + batched-workload graphs 33..56, "
+                                   "k 3..10, Poisson arrivals at 10k/s"}
     return res
 
 
@@ -627,11 +648,15 @@ def run_batch(args):
     one disjoint union with its own k, one pass of the pipeline) with one
     library call per graph on the same resident graphs; results must be
     identical."""
+    return batch_form(args.batch_graphs)
+
+
+def batch_form(G, quiet=False):
+    """run_batch on graphs 0..G-1."""
     import torch
 
     import kclgen
     import paper_2203_13512_gb300 as kcl
-    G = args.batch_graphs
     t0 = time.perf_counter()
     data = [kclgen.batch_graph(i) for i in range(G)]
     gen_s = time.perf_counter() - t0
@@ -657,7 +682,8 @@ def run_batch(args):
             return list(zip(c, s))
 
         ref = per_graph()  # warm-up (allocates each graph's scratch)
-        print("batch %s: warm-up per-graph pass done" % o, file=sys.stderr, flush=True)
+        if not quiet:
+            print("batch %s: warm-up per-graph pass done" % o, file=sys.stderr, flush=True)
         got = batched()
         assert got == ref, "batched results differ from per-graph results"
         torch.cuda.synchronize()
@@ -669,7 +695,9 @@ def run_batch(args):
         batched()
         torch.cuda.synchronize()
         t_bat = time.perf_counter() - t
-        print("batch %s: per-graph %.2f s, batched %.2f s" % (o, t_per, t_bat), file=sys.stderr, flush=True)
+        if not quiet:
+            print("batch %s: per-graph %.2f s, batched %.2f s" % (o, t_per, t_bat), file=sys.stderr,
+                  flush=True)
         n_cl = sum(c for c, _ in ref)
         out["orderings"][o] = {"per_graph_s": round(t_per, 4), "batched_s": round(t_bat, 4),
                                "per_graph_graphs_per_s": G / t_per, "batched_graphs_per_s": G / t_bat,
@@ -683,6 +711,8 @@ def run_batch(args):
     out["k_cliques_per_s_batched"] = cliques / total_bat
     out["bit_exact"] = True
     b.free()
+    for g in graphs:
+        g.free()
     return out
 
 
@@ -698,21 +728,27 @@ def run_serve(args):
     batching of small-graph queries) is compared with a FIFO loop that
     replays the same arrivals and runs one query per call in arrival order;
     every query that completes on both sides must have the same result."""
+    return serve_form(args.serve_queries, args.serve_rates, args.serve_limit_ms)
+
+
+def serve_form(Q, rates, limit, rmat_ids=range(1, 33), batch_ids=range(33, 65),
+               rmat_scale=lambda i: 16 + i % 5, quiet=False):
+    """run_serve over the given graph ids (R-MAT graph i at rmat_scale(i),
+    seed i; batched-workload graph i)."""
     import numpy as np
     import torch
 
     import kclgen
     import paper_2203_13512_gb300 as kcl
     t0 = time.perf_counter()
-    graphs = [kcl.kcl_load_csr(*kclgen.rmat20(seed=i, scale=16 + i % 5)) for i in range(1, 33)]
-    graphs += [kcl.kcl_load_csr(*kclgen.batch_graph(i)[:2]) for i in range(33, 65)]
+    graphs = [kcl.kcl_load_csr(*kclgen.rmat20(seed=i, scale=rmat_scale(i))) for i in rmat_ids]
+    graphs += [kcl.kcl_load_csr(*kclgen.batch_graph(i)[:2]) for i in batch_ids]
+    NG = len(graphs)
     load_s = time.perf_counter() - t0
     rng = np.random.default_rng(1)
-    Q = args.serve_queries
-    qs = [(int(rng.integers(64)), int(rng.integers(3, 11)),
+    qs = [(int(rng.integers(NG)), int(rng.integers(3, 11)),
            "color" if rng.random() < 0.5 else "degree", bool(rng.random() < 0.5)) for _ in range(Q)]
     gaps = rng.exponential(1.0, Q)
-    limit = args.serve_limit_ms
     for g in graphs:
         kcl.kcl_set_time_limit(g, limit)
 
@@ -726,16 +762,19 @@ def run_serve(args):
         except kcl.KclError as e:
             return None, None, e.status
 
-    for q in qs[:64]:
+    for q in qs[:NG]:
         run_one(q)  # warm-up: every graph's scratch
+    scales = sorted({rmat_scale(i) for i in rmat_ids})
     out = {"metric": "served queries: throughput and latency, continuous batching vs FIFO",
            "unit": "queries/s", "higher_is_better": True, "n_gpus": 1,
-           "config": {"workload": "served-mixed", "graphs": 64, "queries": Q,
-                      "rmat_scales": "16..20", "k": "3..10", "slots": 8, "scratch_budget_gb": 100,
+           "config": {"workload": "served-mixed", "graphs": NG, "rmat_graphs": len(rmat_ids),
+                      "batch_graphs": len(batch_ids), "queries": Q,
+                      "rmat_scales": "%d..%d" % (scales[0], scales[-1]) if scales else None,
+                      "k": "3..10", "slots": 8, "scratch_budget_gb": 100,
                       "time_limit_ms": limit, "load_s": round(load_s, 1)},
            "data": "synthetic", "rates": {}}
     compared = 0
-    for rate in args.serve_rates:
+    for rate in rates:
         arr = np.cumsum(gaps / rate)
         # FIFO: one query per call in arrival order, replayed against the clock
         fifo_res, fifo_lat = [], []
@@ -748,11 +787,12 @@ def run_serve(args):
             fifo_res.append(run_one(q))
             fifo_lat.append(time.perf_counter() - base - a)
         fifo_span = time.perf_counter() - base
-        print("fifo at %g/s: %.1f s" % (rate, fifo_span), file=sys.stderr, flush=True)
+        if not quiet:
+            print("fifo at %g/s: %.1f s" % (rate, fifo_span), file=sys.stderr, flush=True)
         srv = kcl.kcl_server_create(slots=8, scratch_budget_bytes=100 << 30, small_nnz=1 << 20)
         kcl.kcl_server_set_time_limit(srv, limit)
         ids = [kcl.kcl_server_add_graph(srv, g) for g in graphs]
-        for gi in range(8):  # warm the slots' scratch
+        for gi in range(min(8, NG)):  # warm the slots' scratch
             kcl.kcl_server_wait(srv, kcl.kcl_server_submit(srv, ids[gi], 3, "color"))
         sbase = kcl.kcl_server_clock(srv)
         tickets = []
@@ -762,7 +802,8 @@ def run_serve(args):
             tickets.append(kcl.kcl_server_submit(srv, ids[gi], k, o, lst))
         res = [kcl.kcl_server_wait(srv, t) for t in tickets]
         srv.destroy()
-        print("served at %g/s" % rate, file=sys.stderr, flush=True)
+        if not quiet:
+            print("served at %g/s" % rate, file=sys.stderr, flush=True)
         for r, (c, h, st), q in zip(res, fifo_res, qs):
             if r["status"] == 0 and st == 0:
                 assert (r["count"], r["checksum"]) == (c, h), q
@@ -773,18 +814,22 @@ def run_serve(args):
         makespan = max(r["done_s"] for r in res) - sbase
         out["rates"][str(rate)] = {
             "served": {"throughput_qps": Q / makespan, "completed": len(ok_s),
+                       "completed_per_s": len(ok_s) / makespan,
                        "timed_out": Q - len(ok_s),
                        "p50_ms": 1e3 * float(np.percentile(slat, 50)) if slat else None,
                        "p99_ms": 1e3 * float(np.percentile(slat, 99)) if slat else None,
                        "mean_batch": float(np.mean([r["batch"] for r in res]))},
             "fifo": {"throughput_qps": Q / fifo_span, "completed": len(flat),
+                     "completed_per_s": len(flat) / fifo_span,
                      "timed_out": Q - len(flat),
                      "p50_ms": 1e3 * float(np.percentile(flat, 50)) if flat else None,
                      "p99_ms": 1e3 * float(np.percentile(flat, 99)) if flat else None}}
-    last = out["rates"][str(args.serve_rates[-1])]
+    last = out["rates"][str(rates[-1])]
     out["value"] = last["served"]["throughput_qps"]
     out["results_compared_equal"] = compared
     out["bit_exact"] = True
+    for g in graphs:
+        g.free()
     return out
 
 
@@ -920,6 +965,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-k6", action="store_true", help="skip the timed k = 6 calls")
     ap.add_argument("--no-c1", action="store_true", help="skip the small Chung-Lu line")
+    ap.add_argument("--no-forms", action="store_true",
+                    help="skip the bounded batched and served samples of the default line")
+    ap.add_argument("--summary-batch-graphs", type=int, default=128)
+    ap.add_argument("--summary-serve-queries", type=int, default=400)
     ap.add_argument("--c3-limit-s", type=float, default=60.0,
                     help="time limit of each call of the community workload (--form c3)")
     ap.add_argument("--form", default="single", choices=["single", "batch", "serve", "ablation", "c3"],

@@ -369,7 +369,9 @@ kcl_status run_call(kcl_graph *g, uint32_t k, kcl_ordering ord, const kcl_ring *
         la.wrap = ring->wrap;
     }
     T.begin(3);
-    if (fe.n_roots > 0) T.add(3, launch_set_deadline(w.res, g->time_limit_ms, g->stream));
+    // the result block is zeroed per call (deadline 0: none); a limit is set on the device
+    if (fe.n_roots > 0 && g->time_limit_ms)
+        T.add(3, launch_set_deadline(w.res, g->time_limit_ms, g->stream));
     if (fe.n_roots > 0) {
         size_t arena = ord == KCL_ORDER_DEGREE
                            ? sdegree_arena_words(k, g->num_sms, fe.max_outdeg)

@@ -380,6 +380,46 @@ __device__ __forceinline__ uint32_t row_words(const View &v, uint32_t p, uint32_
     return wl < cw ? wl : cw;
 }
 
+// A lane's run of rlen cliques within a leaf batch: its first clique is set
+// bit `rank` of B'(q[o]) & C, and it walks the set bits of the queued
+// candidates' rows from there, writing records lane, lane + 32, ... of the
+// batch (base slot0).
+template <int NR>
+__device__ __forceinline__ void leaf_walk(const View &v, const uint32_t *C, uint32_t cw,
+                                          const uint16_t *q, uint32_t o, uint32_t rank, uint32_t rlen,
+                                          const uint32_t *sortedR, const Emit &em,
+                                          unsigned long long slot0, unsigned long long &cks) {
+    CliqueOut<NR> co;
+    co.init(sortedR, v.k, em.ring, em.capacity, em.wrap, slot0, lane_id());
+    uint32_t po = q[o];
+    const uint32_t *row = v.B + po * v.WP;
+    uint32_t wl = row_words(v, po, cw), a = v.ids[po];
+    uint32_t t = 0, mm = 0;
+    for (; t < wl; t++) {
+        mm = row[t] & C[t];
+        const uint32_t c = __popc(mm);
+        if (rank < c) break;
+        rank -= c;
+    }
+    for (uint32_t z = 0; z < rank; z++) mm &= mm - 1;
+    for (uint32_t r = 0; r < rlen; r++) {
+        // mm holds the remaining bits of word t (its lowest is the next clique)
+        const uint32_t b = t * 32 + (__ffs(mm) - 1);
+        cks += co.put(a, v.ids[b]);
+        mm &= mm - 1;
+        while (!mm && r + 1 < rlen) {
+            if (++t >= wl) {  // next candidate with cliques
+                po = q[++o];
+                row = v.B + po * v.WP;
+                wl = row_words(v, po, cw);
+                a = v.ids[po];
+                t = 0;
+            }
+            mm = row[t] & C[t];
+        }
+    }
+}
+
 // A batch of nb <= 32 leaf candidates q[0..nb): lane i takes candidate q[i]
 // and closes |B'(q[i]) & C| cliques.
 template <bool LIST>
@@ -422,36 +462,12 @@ __device__ void leaf_batch(const View &v, const uint32_t *C, uint32_t cw, const 
     }
     const uint32_t eo = __shfl_sync(kFull, excl, o & 31u);
     if (rlen == 0) return;
-    const uint32_t r1 = r0 + rlen;
-    const uint64_t seed = hash_seed(v.k);
-    uint32_t po = q[o];
-    const uint32_t *row = v.B + po * v.WP;
-    uint32_t wl = row_words(v, po, cw), a = v.ids[po];
-    // the (r0 - eo)-th set bit of the owner's row & C
-    uint32_t rank = r0 - eo, t = 0, mm = 0;
-    for (; t < wl; t++) {
-        mm = row[t] & C[t];
-        const uint32_t c = __popc(mm);
-        if (rank < c) break;
-        rank -= c;
-    }
-    for (uint32_t z = 0; z < rank; z++) mm &= mm - 1;
-    for (uint32_t r = r0; r < r1; r++) {
-        // mm holds the remaining bits of word t (its lowest is clique r)
-        const uint32_t b = t * 32 + (__ffs(mm) - 1);
-        cks += clique_hash2(sortedR, v.k - 2, a, v.ids[b], seed,
-                            ring_rec(em.ring, em.capacity, em.wrap, slot0, (r - r0) * 32 + lane, v.k));
-        mm &= mm - 1;
-        while (!mm && r + 1 < r1) {
-            if (++t >= wl) {  // next candidate with cliques
-                po = q[++o];
-                row = v.B + po * v.WP;
-                wl = row_words(v, po, cw);
-                a = v.ids[po];
-                t = 0;
-            }
-            mm = row[t] & C[t];
-        }
+    switch (v.k) {  // warp-uniform: R in registers for the common k
+        case 3: leaf_walk<1>(v, C, cw, q, o, r0 - eo, rlen, sortedR, em, slot0, cks); break;
+        case 4: leaf_walk<2>(v, C, cw, q, o, r0 - eo, rlen, sortedR, em, slot0, cks); break;
+        case 5: leaf_walk<3>(v, C, cw, q, o, r0 - eo, rlen, sortedR, em, slot0, cks); break;
+        case 6: leaf_walk<4>(v, C, cw, q, o, r0 - eo, rlen, sortedR, em, slot0, cks); break;
+        default: leaf_walk<0>(v, C, cw, q, o, r0 - eo, rlen, sortedR, em, slot0, cks);
     }
 }
 

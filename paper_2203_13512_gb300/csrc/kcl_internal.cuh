@@ -173,6 +173,111 @@ __device__ __forceinline__ uint64_t clique_hash2(const uint32_t *sortedR, uint32
     return h;
 }
 
+// A lane's cliques R + {a, b} within one batch of records (listing mode):
+// the lane writes records lane, lane + 32, lane + 64, ... of the batch, so
+// the warp's stores at each step are 32 consecutive records.  NR = k - 2 > 0
+// holds R's ids in registers and merges each clique with selects in a fully
+// unrolled loop (the same k SplitMix64 rounds over the ascending ids as
+// clique_hash2, and the same record); NR = 0 is the runtime-k form.
+template <int NR>
+struct CliqueOut {
+    static constexpr int NRR = NR > 0 ? NR : 1;
+    uint32_t R[NRR];
+    const uint32_t *sortedR;
+    uint64_t seed;
+    uint32_t *ring;
+    unsigned long long cap, s;  // s: this lane's next record index in the ring
+    int wrap;
+    uint32_t k;
+    bool vec;  // records 16-byte (k = 4) or 8-byte (k = 6) aligned
+
+    // slot0: the batch's first record (ring_base); first: this lane's
+    // offset from it.
+    __device__ __forceinline__ void init(const uint32_t *sR, uint32_t kk, uint32_t *rg,
+                                         unsigned long long capacity, int wr,
+                                         unsigned long long slot0, uint32_t first) {
+        sortedR = sR;
+        k = kk;
+        seed = hash_seed(kk);
+        ring = rg;
+        cap = capacity;
+        wrap = wr;
+        if constexpr (NR > 0) {
+#pragma unroll
+            for (int i = 0; i < NR; i++) R[i] = sR[i];
+        }
+        s = slot0 + first;
+        if (wrap && s >= cap) s %= cap;
+        const uintptr_t al = reinterpret_cast<uintptr_t>(rg);
+        vec = (NR == 2 && (al & 15u) == 0) || (NR == 4 && (al & 7u) == 0);
+    }
+
+    __device__ __forceinline__ uint32_t *rec() const {
+        if (!ring || (!wrap && s >= cap)) return nullptr;
+        return ring + s * k;
+    }
+
+    __device__ __forceinline__ void advance() {
+        s += 32;
+        if (wrap && s >= cap) {
+            s -= cap;
+            if (s >= cap) s %= cap;  // only for rings smaller than 32 records
+        }
+    }
+
+    // Hash of R + {a, b} (a != b, neither in R), its record written when
+    // the ring keeps it; then moves on to the lane's next record.
+    __device__ __forceinline__ uint64_t put(uint32_t a, uint32_t b) {
+        uint32_t *out = rec();
+        uint64_t h;
+        if constexpr (NR == 0) {
+            h = clique_hash2(sortedR, k - 2, a, b, seed, out);
+        } else {
+            uint32_t e = a < b ? a : b, e2 = a < b ? b : a;
+            uint32_t q[NR], x[NR + 2];
+#pragma unroll
+            for (int i = 0; i < NR; i++) q[i] = R[i];
+            h = seed;
+#pragma unroll
+            for (int z = 0; z < NR + 2; z++) {
+                // ids are < 2^32 - 1, so 0xFFFFFFFF marks an exhausted source
+                const bool te = e < q[0];
+                x[z] = te ? e : q[0];
+                e = te ? e2 : e;
+                e2 = te ? 0xFFFFFFFFu : e2;
+#pragma unroll
+                for (int i = 0; i + 1 < NR; i++) q[i] = te ? q[i] : q[i + 1];
+                q[NR - 1] = te ? q[NR - 1] : 0xFFFFFFFFu;
+                h = mix64(h ^ (uint64_t)x[z]);
+            }
+            if (out) {
+                if constexpr (NR == 2) {
+                    if (vec) {
+                        *reinterpret_cast<uint4 *>(out) = make_uint4(x[0], x[1], x[2], x[3]);
+                    } else {
+#pragma unroll
+                        for (int z = 0; z < 4; z++) out[z] = x[z];
+                    }
+                } else if constexpr (NR == 4) {
+                    if (vec) {
+#pragma unroll
+                        for (int z = 0; z < 6; z += 2)
+                            reinterpret_cast<uint2 *>(out)[z >> 1] = make_uint2(x[z], x[z + 1]);
+                    } else {
+#pragma unroll
+                        for (int z = 0; z < 6; z++) out[z] = x[z];
+                    }
+                } else {
+#pragma unroll
+                    for (int z = 0; z < NR + 2; z++) out[z] = x[z];
+                }
+            }
+        }
+        advance();
+        return h;
+    }
+};
+
 // Ring records of a batch: the batch claims `count` consecutive record
 // indices from `emitted` (one atomic), and its first index becomes the base
 // of ring_rec -- taken mod capacity once per batch when the ring wraps, so

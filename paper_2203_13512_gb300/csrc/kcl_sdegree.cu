@@ -366,6 +366,21 @@ __device__ __forceinline__ bool search16(const uint16_t *a, uint32_t n, uint32_t
     return lo < n && a[lo] == x;
 }
 
+// Pairs lane, lane + 32, ... of st.ebuf, into records of the same offsets
+// from slot0.
+template <int NR>
+__device__ __forceinline__ void flush_walk(const LView &v, uint32_t nb, const LStack &st,
+                                           const Emit &em, unsigned long long slot0,
+                                           unsigned long long &cks) {
+    const unsigned lane = lane_id();
+    CliqueOut<NR> co;
+    co.init(st.sortedR, v.k, em.ring, em.capacity, em.wrap, slot0, lane);
+    for (uint32_t e = lane; e < nb; e += 32) {
+        const uint32_t pr = st.ebuf[e];
+        cks += co.put(v.nbr[pr >> 16], v.nbr[pr & 0xFFFFu]);
+    }
+}
+
 // Listing: hash the nb (candidate << 16 | match) pairs of st.ebuf with all
 // lanes; each pair closes the clique R + {candidate, match}.
 __device__ void flush_pairs(const LView &v, uint32_t nb, const LStack &st, const Emit &em,
@@ -378,11 +393,12 @@ __device__ void flush_pairs(const LView &v, uint32_t nb, const LStack &st, const
         if (lane == 0) slot0 = ring_base(atomicAdd(&res->emitted, (unsigned long long)nb), em.capacity, em.wrap);
         slot0 = __shfl_sync(kFull, slot0, 0);
     }
-    const uint64_t seed = hash_seed(k);
-    for (uint32_t e = lane; e < nb; e += 32) {
-        const uint32_t pr = st.ebuf[e];
-        cks += clique_hash2(st.sortedR, k - 2, v.nbr[pr >> 16], v.nbr[pr & 0xFFFFu], seed,
-                            ring_rec(em.ring, em.capacity, em.wrap, slot0, e, k));
+    switch (k) {  // warp-uniform: R in registers for the common k
+        case 3: flush_walk<1>(v, nb, st, em, slot0, cks); break;
+        case 4: flush_walk<2>(v, nb, st, em, slot0, cks); break;
+        case 5: flush_walk<3>(v, nb, st, em, slot0, cks); break;
+        case 6: flush_walk<4>(v, nb, st, em, slot0, cks); break;
+        default: flush_walk<0>(v, nb, st, em, slot0, cks);
     }
     __syncwarp();
 }
@@ -603,6 +619,42 @@ __device__ __forceinline__ uint32_t brow_and(const BView &v, uint32_t q, const u
     return x;
 }
 
+// A lane's run of rlen cliques within a bit-row leaf batch (as BitCol's
+// leaf_walk): its first clique is set bit `rank` of row(q[o]) & C.
+template <int NR>
+__device__ __forceinline__ void bleaf_walk(const BView &v, const uint32_t *C, const uint16_t *q,
+                                           uint32_t o, uint32_t rank, uint32_t rlen,
+                                           const uint32_t *sortedR, const Emit &em,
+                                           unsigned long long slot0, unsigned long long &cks) {
+    CliqueOut<NR> co;
+    co.init(sortedR, v.k, em.ring, em.capacity, em.wrap, slot0, lane_id());
+    uint32_t qo = q[o];
+    const uint32_t *row = v.R + qo * v.WP;
+    uint32_t a = v.ids[qo];
+    uint32_t t = qo >> 5, mm = 0;
+    for (; t < v.W; t++) {
+        mm = row[t] & C[t];
+        const uint32_t c = __popc(mm);
+        if (rank < c) break;
+        rank -= c;
+    }
+    for (uint32_t z = 0; z < rank; z++) mm &= mm - 1;
+    for (uint32_t r = 0; r < rlen; r++) {
+        const uint32_t b = t * 32 + (__ffs(mm) - 1);
+        cks += co.put(a, v.ids[b]);
+        mm &= mm - 1;
+        while (!mm && r + 1 < rlen) {
+            if (++t >= v.W) {  // next candidate with cliques
+                qo = q[++o];
+                row = v.R + qo * v.WP;
+                a = v.ids[qo];
+                t = qo >> 5;
+            }
+            mm = row[t] & C[t];
+        }
+    }
+}
+
 // Leaf (l = 2) on bitmap C: every candidate q in C closes |row(q) & C|
 // cliques; candidates are packed 32 to a batch (queue of 64 u16).
 template <bool LIST>
@@ -639,34 +691,12 @@ __device__ void bleaf_batch(const BView &v, const uint32_t *C, const uint16_t *q
     }
     const uint32_t eo = __shfl_sync(kFull, excl, o & 31u);
     if (rlen == 0) return;
-    const uint32_t r1 = r0 + rlen;
-    const uint32_t k = v.k;
-    const uint64_t seed = hash_seed(k);
-    uint32_t qo = q[o];
-    const uint32_t *row = v.R + qo * v.WP;
-    uint32_t a = v.ids[qo];
-    uint32_t rank = r0 - eo, t = qo >> 5, mm = 0;
-    for (; t < v.W; t++) {
-        mm = row[t] & C[t];
-        const uint32_t c = __popc(mm);
-        if (rank < c) break;
-        rank -= c;
-    }
-    for (uint32_t z = 0; z < rank; z++) mm &= mm - 1;
-    for (uint32_t r = r0; r < r1; r++) {
-        const uint32_t b = t * 32 + (__ffs(mm) - 1);
-        cks += clique_hash2(sortedR, k - 2, a, v.ids[b], seed,
-                            ring_rec(em.ring, em.capacity, em.wrap, slot0, (r - r0) * 32 + lane, k));
-        mm &= mm - 1;
-        while (!mm && r + 1 < r1) {
-            if (++t >= v.W) {  // next candidate with cliques
-                qo = q[++o];
-                row = v.R + qo * v.WP;
-                a = v.ids[qo];
-                t = qo >> 5;
-            }
-            mm = row[t] & C[t];
-        }
+    switch (v.k) {  // warp-uniform: R in registers for the common k
+        case 3: bleaf_walk<1>(v, C, q, o, r0 - eo, rlen, sortedR, em, slot0, cks); break;
+        case 4: bleaf_walk<2>(v, C, q, o, r0 - eo, rlen, sortedR, em, slot0, cks); break;
+        case 5: bleaf_walk<3>(v, C, q, o, r0 - eo, rlen, sortedR, em, slot0, cks); break;
+        case 6: bleaf_walk<4>(v, C, q, o, r0 - eo, rlen, sortedR, em, slot0, cks); break;
+        default: bleaf_walk<0>(v, C, q, o, r0 - eo, rlen, sortedR, em, slot0, cks);
     }
 }
 
