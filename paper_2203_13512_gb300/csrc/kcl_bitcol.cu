@@ -562,8 +562,7 @@ __device__ void expand(const View &v, const uint32_t *C, uint32_t cw, uint32_t l
 // cliques (one three-input AND per word; the rows lie below q, so the batch
 // reads a uniform number of words up to its largest q).
 __device__ __forceinline__ void pair_batch(const View &v, const uint32_t *C, uint32_t cw,
-                                           const uint32_t *pq, uint32_t nb,
-                                           unsigned long long &cnt) {
+                                           const uint32_t *pq, uint32_t nb, uint32_t &acc) {
     const unsigned lane = lane_id();
     const uint32_t e = pq[lane < nb ? lane : nb - 1];
     const uint32_t p = e >> 16, q = e & 0xFFFFu;
@@ -575,6 +574,7 @@ __device__ __forceinline__ void pair_batch(const View &v, const uint32_t *C, uin
         const uint4 *a4 = reinterpret_cast<const uint4 *>(rq);
         const uint4 *b4 = reinterpret_cast<const uint4 *>(rp);
         const uint4 *c4 = reinterpret_cast<const uint4 *>(C);
+#pragma unroll 2
         for (uint32_t t = 0; t < nc; t++) {
             const uint4 a = a4[t], b = b4[t], c = c4[t];
             x += __popc(a.x & b.x & c.x) + __popc(a.y & b.y & c.y) + __popc(a.z & b.z & c.z) +
@@ -584,7 +584,24 @@ __device__ __forceinline__ void pair_batch(const View &v, const uint32_t *C, uin
         const uint32_t nw = min((qmax >> 5) + 1, cw);
         for (uint32_t t = 0; t < nw; t++) x += __popc(rq[t] & rp[t] & C[t]);
     }
-    if (lane < nb) cnt += x;
+    acc += lane < nb ? x : 0u;
+}
+
+// The pair queue: 64 entries (the leaf region of a warp's stack).
+constexpr uint32_t kPairQueue = 64;
+
+// Runs full batches while the queue holds 32 pairs or more (pend <= 64).
+__device__ __forceinline__ void pair_drain(const View &v, const uint32_t *C, uint32_t cw,
+                                           uint32_t *pq, uint32_t &pend, uint32_t &acc) {
+    const unsigned lane = lane_id();
+    while (pend >= 32) {
+        __syncwarp();
+        pair_batch(v, C, cw, pq, 32, acc);
+        __syncwarp();
+        if (lane < pend - 32) pq[lane] = pq[32 + lane];
+        pend -= 32;
+        __syncwarp();
+    }
 }
 
 // Counting below a level-3 node with candidate set C and pending children P
@@ -593,7 +610,11 @@ __device__ __forceinline__ void pair_batch(const View &v, const uint32_t *C, uin
 // pairs of the node go through one per-warp queue of 64 entries (pq), 32 to
 // a batch, so no child materialises its C' and batches stay full across
 // children.  Cm (W words of scratch) receives C restricted to colour >= 2,
-// the leaf candidates, so the pair scan reads four masked words at a time.
+// the leaf candidates, so the pair scan reads four masked words at a time
+// and queues their pairs in one step when they fit (each lane its bit of
+// each word, at the word's prefix count).  The per-lane sum stays 32-bit
+// within the node: at most d^2 / 32 pairs of at most d cliques per lane,
+// below 2^31 for d <= 4096 (the largest class).
 __device__ void leaf_pairs(const View &v, const uint32_t *C, uint32_t cw, const uint32_t *P,
                            uint32_t *Cm, uint32_t *pq, unsigned long long &cnt) {
     const unsigned lane = lane_id();
@@ -601,7 +622,7 @@ __device__ void leaf_pairs(const View &v, const uint32_t *C, uint32_t cw, const 
     for (uint32_t t = lane; t < v.W; t += 32) Cm[t] = t < cw ? cand_word(C, t, s2) : 0u;
     __syncwarp();
     const unsigned lt = (1u << lane) - 1u, me = 1u << lane;
-    uint32_t pend = 0;
+    uint32_t pend = 0, acc = 0;
     for (uint32_t jp = s2 >> 5; jp < cw; jp++) {
         uint32_t pw = P[jp];
         while (pw) {
@@ -619,20 +640,25 @@ __device__ void leaf_pairs(const View &v, const uint32_t *C, uint32_t cw, const 
 #pragma unroll
                     for (int z = 0; z < 4; z++) mw[z] = t0 + z < ncw ? rowp[t0 + z] & Cm[t0 + z] : 0u;
                 }
-#pragma unroll
-                for (int z = 0; z < 4; z++) {
-                    const uint32_t m = mw[z];
-                    if (!m) continue;
-                    const uint32_t base = (p << 16) | ((t0 + z) * 32);
-                    if (m & me) pq[pend + __popc(m & lt)] = base + lane;
-                    pend += __popc(m);
-                    if (pend >= 32) {
-                        __syncwarp();
-                        pair_batch(v, C, cw, pq, 32, cnt);
-                        __syncwarp();
-                        if (lane < pend - 32) pq[lane] = pq[32 + lane];
-                        pend -= 32;
-                        __syncwarp();
+                const uint32_t c0 = __popc(mw[0]), c1 = __popc(mw[1]), c2 = __popc(mw[2]),
+                               c3 = __popc(mw[3]);
+                const uint32_t tot = c0 + c1 + c2 + c3;
+                const uint32_t b0 = (p << 16) | (t0 * 32 + lane);
+                if (pend + tot <= kPairQueue) {
+                    const uint32_t o1 = pend + c0, o2 = o1 + c1, o3 = o2 + c2;
+                    if (mw[0] & me) pq[pend + __popc(mw[0] & lt)] = b0;
+                    if (mw[1] & me) pq[o1 + __popc(mw[1] & lt)] = b0 + 32;
+                    if (mw[2] & me) pq[o2 + __popc(mw[2] & lt)] = b0 + 64;
+                    if (mw[3] & me) pq[o3 + __popc(mw[3] & lt)] = b0 + 96;
+                    pend += tot;
+                    pair_drain(v, C, cw, pq, pend, acc);
+                } else {  // dense words: one at a time (each adds at most 32)
+#pragma unroll 1
+                    for (int z = 0; z < 4; z++) {
+                        const uint32_t m = mw[z];
+                        if (m & me) pq[pend + __popc(m & lt)] = b0 + 32 * z;
+                        pend += __popc(m);
+                        pair_drain(v, C, cw, pq, pend, acc);
                     }
                 }
             }
@@ -640,9 +666,10 @@ __device__ void leaf_pairs(const View &v, const uint32_t *C, uint32_t cw, const 
     }
     if (pend) {
         __syncwarp();
-        pair_batch(v, C, cw, pq, pend, cnt);
+        pair_batch(v, C, cw, pq, pend, acc);
         __syncwarp();
     }
+    cnt += acc;
 }
 
 // The subtree below first-level child p0 of the root (C1 = B'(p0)), run by

@@ -758,7 +758,7 @@ __device__ void bexpand(const BView &v, const uint32_t *C, uint32_t l, uint32_t 
 // |row(q) & row(p) & C| cliques.  Rows lie above their vertex, so the batch
 // reads a uniform range of words from its smallest q on.
 __device__ __forceinline__ void bpair_batch(const BView &v, const uint32_t *C, const uint32_t *pq,
-                                            uint32_t nb, unsigned long long &cnt) {
+                                            uint32_t nb, uint32_t &acc) {
     const unsigned lane = lane_id();
     const uint32_t e = pq[lane < nb ? lane : nb - 1];
     const uint32_t p = e >> 16, q = e & 0xFFFFu;
@@ -768,6 +768,7 @@ __device__ __forceinline__ void bpair_batch(const BView &v, const uint32_t *C, c
         const uint4 *a4 = reinterpret_cast<const uint4 *>(v.R + q * v.WP);
         const uint4 *b4 = reinterpret_cast<const uint4 *>(v.R + p * v.WP);
         const uint4 *c4 = reinterpret_cast<const uint4 *>(C);
+#pragma unroll 2
         for (uint32_t t = qmin >> 7; t < (v.W >> 2); t++) {
             const uint4 a = a4[t], b = b4[t], c = c4[t];
             x += __popc(a.x & b.x & c.x) + __popc(a.y & b.y & c.y) + __popc(a.z & b.z & c.z) +
@@ -777,46 +778,83 @@ __device__ __forceinline__ void bpair_batch(const BView &v, const uint32_t *C, c
         const uint32_t *rq = v.R + q * v.WP, *rp = v.R + p * v.WP;
         for (uint32_t t = qmin >> 5; t < v.W; t++) x += __popc(rq[t] & rp[t] & C[t]);
     }
-    if (lane < nb) cnt += x;
+    acc += lane < nb ? x : 0u;
+}
+
+// Runs full batches while the queue holds 32 pairs or more (pend <= 64).
+__device__ __forceinline__ void bpair_drain(const BView &v, const uint32_t *C, uint32_t *pq,
+                                            uint32_t &pend, uint32_t &acc) {
+    const unsigned lane = lane_id();
+    while (pend >= 32) {
+        __syncwarp();
+        bpair_batch(v, C, pq, 32, acc);
+        __syncwarp();
+        if (lane < pend - 32) pq[lane] = pq[32 + lane];
+        pend -= 32;
+        __syncwarp();
+    }
 }
 
 // Counting below a level-3 node on bit-rows (Algorithm 5 at levels 3 and 2):
 // for every pending child p and every q in row(p) & C, |row(q) & row(p) & C|
 // cliques close.  All (p, q) pairs go through the per-warp queue pq (64
-// entries), 32 to a batch, so no child materialises its C'.
+// entries), 32 to a batch, so no child materialises its C'.  With 16-byte
+// rows the scan reads four words at a time (a row is zero below its
+// vertex, so the chunk may start below it) and queues their pairs in one
+// step when they fit.  The per-lane sum stays 32-bit within the node: at
+// most d^2 / 32 pairs of at most d cliques per lane, and the rows (d^2 / 8
+// bytes) sit in shared memory, so d < 2048 and the sum stays below 2^28.
 __device__ void bleaf_pairs(const BView &v, const uint32_t *C, const uint32_t *P, uint32_t *pq,
                             unsigned long long &cnt) {
     const unsigned lane = lane_id();
     const unsigned lt = (1u << lane) - 1u, me = 1u << lane;
-    uint32_t pend = 0;
+    const bool vec = ((v.W | v.WP) & 3u) == 0;
+    uint32_t pend = 0, acc = 0;
     for (uint32_t jp = 0; jp < v.W; jp++) {
         uint32_t pw = P[jp];
         while (pw) {
             const uint32_t p = jp * 32 + (__ffs(pw) - 1);
             pw &= pw - 1;
             const uint32_t *rowp = v.R + p * v.WP;
-            for (uint32_t t = p >> 5; t < v.W; t++) {  // row(p) lies above p
-                const uint32_t m = rowp[t] & C[t];
-                if (!m) continue;
-                const uint32_t base = (p << 16) | (t * 32);
-                if (m & me) pq[pend + __popc(m & lt)] = base + lane;
-                pend += __popc(m);
-                if (pend >= 32) {
-                    __syncwarp();
-                    bpair_batch(v, C, pq, 32, cnt);
-                    __syncwarp();
-                    if (lane < pend - 32) pq[lane] = pq[32 + lane];
-                    pend -= 32;
-                    __syncwarp();
+            for (uint32_t t0 = vec ? ((p >> 5) & ~3u) : (p >> 5); t0 < v.W; t0 += vec ? 4u : 1u) {
+                uint32_t mw[4] = {0u, 0u, 0u, 0u};
+                if (vec) {
+                    const uint4 a = *reinterpret_cast<const uint4 *>(rowp + t0);
+                    const uint4 c = *reinterpret_cast<const uint4 *>(C + t0);
+                    mw[0] = a.x & c.x; mw[1] = a.y & c.y; mw[2] = a.z & c.z; mw[3] = a.w & c.w;
+                } else {
+                    mw[0] = rowp[t0] & C[t0];
+                }
+                const uint32_t c0 = __popc(mw[0]), c1 = __popc(mw[1]), c2 = __popc(mw[2]),
+                               c3 = __popc(mw[3]);
+                const uint32_t tot = c0 + c1 + c2 + c3;
+                const uint32_t b0 = (p << 16) | (t0 * 32 + lane);
+                if (pend + tot <= 64) {
+                    const uint32_t o1 = pend + c0, o2 = o1 + c1, o3 = o2 + c2;
+                    if (mw[0] & me) pq[pend + __popc(mw[0] & lt)] = b0;
+                    if (mw[1] & me) pq[o1 + __popc(mw[1] & lt)] = b0 + 32;
+                    if (mw[2] & me) pq[o2 + __popc(mw[2] & lt)] = b0 + 64;
+                    if (mw[3] & me) pq[o3 + __popc(mw[3] & lt)] = b0 + 96;
+                    pend += tot;
+                    bpair_drain(v, C, pq, pend, acc);
+                } else {  // dense words: one at a time (each adds at most 32)
+#pragma unroll 1
+                    for (int z = 0; z < 4; z++) {
+                        const uint32_t m = mw[z];
+                        if (m & me) pq[pend + __popc(m & lt)] = b0 + 32 * z;
+                        pend += __popc(m);
+                        bpair_drain(v, C, pq, pend, acc);
+                    }
                 }
             }
         }
     }
     if (pend) {
         __syncwarp();
-        bpair_batch(v, C, pq, pend, cnt);
+        bpair_batch(v, C, pq, pend, acc);
         __syncwarp();
     }
+    cnt += acc;
 }
 
 // The subtree below first-level child p0 (C1 = row(p0)), one warp.
