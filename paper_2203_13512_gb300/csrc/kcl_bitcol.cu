@@ -557,16 +557,12 @@ __device__ void expand(const View &v, const uint32_t *C, uint32_t cw, uint32_t l
     __syncwarp();
 }
 
-// A batch of nb <= 32 (child, candidate) pairs of a level-3 node (counting):
-// lane i takes pair pq[i] = (p << 16) | q and closes |B'(q) & B'(p) & C|
-// cliques (one three-input AND per word; the rows lie below q, so the batch
-// reads a uniform number of words up to its largest q).
-__device__ __forceinline__ void pair_batch(const View &v, const uint32_t *C, uint32_t cw,
-                                           const uint32_t *pq, uint32_t nb, uint32_t &acc) {
-    const unsigned lane = lane_id();
-    const uint32_t e = pq[lane < nb ? lane : nb - 1];
-    const uint32_t p = e >> 16, q = e & 0xFFFFu;
-    const uint32_t qmax = __reduce_max_sync(kFull, q);
+// |B'(q) & B'(p) & C| for lane pairs (p, q) held in registers (has: the lane
+// holds one); the rows lie below q, so all lanes read the words up to the
+// largest q.
+__device__ __forceinline__ void pair_round(const View &v, const uint32_t *C, uint32_t cw, bool has,
+                                           uint32_t p, uint32_t q, uint32_t &acc) {
+    const uint32_t qmax = __reduce_max_sync(kFull, has ? q : 0u);
     const uint32_t *rq = v.B + q * v.WP, *rp = v.B + p * v.WP;
     uint32_t x = 0;
     if (v.W >= 4) {
@@ -584,90 +580,78 @@ __device__ __forceinline__ void pair_batch(const View &v, const uint32_t *C, uin
         const uint32_t nw = min((qmax >> 5) + 1, cw);
         for (uint32_t t = 0; t < nw; t++) x += __popc(rq[t] & rp[t] & C[t]);
     }
-    acc += lane < nb ? x : 0u;
-}
-
-// The pair queue: 64 entries (the leaf region of a warp's stack).
-constexpr uint32_t kPairQueue = 64;
-
-// Runs full batches while the queue holds 32 pairs or more (pend <= 64).
-__device__ __forceinline__ void pair_drain(const View &v, const uint32_t *C, uint32_t cw,
-                                           uint32_t *pq, uint32_t &pend, uint32_t &acc) {
-    const unsigned lane = lane_id();
-    while (pend >= 32) {
-        __syncwarp();
-        pair_batch(v, C, cw, pq, 32, acc);
-        __syncwarp();
-        if (lane < pend - 32) pq[lane] = pq[32 + lane];
-        pend -= 32;
-        __syncwarp();
-    }
+    acc += has ? x : 0u;
 }
 
 // Counting below a level-3 node with candidate set C and pending children P
 // (Algorithm 6 at levels 3 and 2): for every child p and every q in
-// B'(p) & C of colour >= 2, |B'(q) & B'(p) & C| cliques close.  All (p, q)
-// pairs of the node go through one per-warp queue of 64 entries (pq), 32 to
-// a batch, so no child materialises its C' and batches stay full across
-// children.  Cm (W words of scratch) receives C restricted to colour >= 2,
-// the leaf candidates, so the pair scan reads four masked words at a time
-// and queues their pairs in one step when they fit (each lane its bit of
-// each word, at the word's prefix count).  The per-lane sum stays 32-bit
-// within the node: at most d^2 / 32 pairs of at most d cliques per lane,
-// below 2^31 for d <= 4096 (the largest class).
+// B'(p) & C of colour >= 2, |B'(q) & B'(p) & C| cliques close.  The words
+// of B'(p) & Cm (Cm: C restricted to colour >= 2, the leaf candidates) for
+// all children p form a stream of items (p, t); each lane holds one item's
+// remaining bits and, every round, turns its lowest bit q into the pair
+// (p, q), so a round is a batch of up to 32 pairs built in registers.  A lane
+// whose word runs out takes the next item from a 64-entry ring (ibuf), which
+// the warp refills with up to 32 words of the next child at a time.  The
+// per-lane sum stays 32-bit within the node: at most d^2 / 32 pairs of at
+// most d cliques per lane, below 2^31 for d <= 4096 (the largest class).
 __device__ void leaf_pairs(const View &v, const uint32_t *C, uint32_t cw, const uint32_t *P,
-                           uint32_t *Cm, uint32_t *pq, unsigned long long &cnt) {
+                           uint32_t *Cm, uint32_t *ibuf, unsigned long long &cnt) {
     const unsigned lane = lane_id();
     const uint32_t s2 = start_of(v, 2);
     for (uint32_t t = lane; t < v.W; t += 32) Cm[t] = t < cw ? cand_word(C, t, s2) : 0u;
     __syncwarp();
-    const unsigned lt = (1u << lane) - 1u, me = 1u << lane;
-    uint32_t pend = 0, acc = 0;
-    for (uint32_t jp = s2 >> 5; jp < cw; jp++) {
-        uint32_t pw = P[jp];
-        while (pw) {
-            const uint32_t p = jp * 32 + (__ffs(pw) - 1);
-            pw &= pw - 1;
-            const uint32_t ncw = min(cw, (p >> 5) + 1);  // B'(p) lies below p
-            const uint32_t *rowp = v.B + p * v.WP;
-            for (uint32_t t0 = 0; t0 < ncw; t0 += 4) {
-                uint32_t mw[4];
-                if (v.W >= 4) {
-                    const uint4 a = *reinterpret_cast<const uint4 *>(rowp + t0);
-                    const uint4 c = *reinterpret_cast<const uint4 *>(Cm + t0);
-                    mw[0] = a.x & c.x; mw[1] = a.y & c.y; mw[2] = a.z & c.z; mw[3] = a.w & c.w;
-                } else {
-#pragma unroll
-                    for (int z = 0; z < 4; z++) mw[z] = t0 + z < ncw ? rowp[t0 + z] & Cm[t0 + z] : 0u;
+    const unsigned lt = (1u << lane) - 1u;
+    // producer (warp-uniform): child word jp / bits pw, current child cp with
+    // its next word ct of cn; ring ibuf[head..tail) (indices mod 64)
+    uint32_t jp = s2 >> 5, pw = jp < cw ? P[jp] : 0u, cp = 0, ct = 0, cn = 0;
+    uint32_t head = 0, tail = 0;
+    // lane: remaining bits m of word t (bit offset tb) of child p
+    uint32_t m = 0, p = 0, tb = 0, acc = 0;
+    bool more = true;  // items may remain
+    for (;;) {
+        // give every lane without bits a new word while items remain
+        while (more) {
+            const unsigned need = __ballot_sync(kFull, m == 0);
+            if (!need) break;
+            const uint32_t nneed = __popc(need);
+            while (tail - head < nneed) {
+                if (ct >= cn) {  // next child
+                    while (!pw && jp + 1 < cw) pw = P[++jp];
+                    if (!pw) break;
+                    cp = jp * 32 + (__ffs(pw) - 1);
+                    pw &= pw - 1;
+                    ct = 0;
+                    cn = min(cw, (cp >> 5) + 1);  // B'(p) lies below p
                 }
-                const uint32_t c0 = __popc(mw[0]), c1 = __popc(mw[1]), c2 = __popc(mw[2]),
-                               c3 = __popc(mw[3]);
-                const uint32_t tot = c0 + c1 + c2 + c3;
-                const uint32_t b0 = (p << 16) | (t0 * 32 + lane);
-                if (pend + tot <= kPairQueue) {
-                    const uint32_t o1 = pend + c0, o2 = o1 + c1, o3 = o2 + c2;
-                    if (mw[0] & me) pq[pend + __popc(mw[0] & lt)] = b0;
-                    if (mw[1] & me) pq[o1 + __popc(mw[1] & lt)] = b0 + 32;
-                    if (mw[2] & me) pq[o2 + __popc(mw[2] & lt)] = b0 + 64;
-                    if (mw[3] & me) pq[o3 + __popc(mw[3] & lt)] = b0 + 96;
-                    pend += tot;
-                    pair_drain(v, C, cw, pq, pend, acc);
-                } else {  // dense words: one at a time (each adds at most 32)
-#pragma unroll 1
-                    for (int z = 0; z < 4; z++) {
-                        const uint32_t m = mw[z];
-                        if (m & me) pq[pend + __popc(m & lt)] = b0 + 32 * z;
-                        pend += __popc(m);
-                        pair_drain(v, C, cw, pq, pend, acc);
-                    }
+                const uint32_t nt = min(cn - ct, 32u);
+                if (lane < nt) ibuf[(tail + lane) & 63u] = (cp << 16) | (ct + lane);
+                tail += nt;
+                ct += nt;
+                __syncwarp();
+            }
+            const uint32_t avail = min(tail - head, nneed);
+            if (avail < nneed) more = false;  // the stream is exhausted
+            if (m == 0) {
+                const uint32_t r = __popc(need & lt);
+                if (r < avail) {
+                    const uint32_t it = ibuf[(head + r) & 63u];
+                    p = it >> 16;
+                    const uint32_t t = it & 0xFFFFu;
+                    m = v.B[p * v.WP + t] & Cm[t];
+                    tb = t * 32;
                 }
             }
+            head += avail;
+            __syncwarp();
         }
-    }
-    if (pend) {
-        __syncwarp();
-        pair_batch(v, C, cw, pq, pend, acc);
-        __syncwarp();
+        const bool has = m != 0;
+        if (!__any_sync(kFull, has)) break;
+        uint32_t q = 0;
+        if (has) {
+            q = tb + (__ffs(m) - 1);
+            m &= m - 1;
+        }
+        pair_round(v, C, cw, has, p, q, acc);
     }
     cnt += acc;
 }
