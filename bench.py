@@ -507,8 +507,9 @@ KERNEL_NAMES = {
 # changes, until a new capture exists.
 _DRAM = "profiles/k_bitcol_cta_rmat20.md"
 TRAFFIC = {
-    (5, "color", "count", 4): (30.727e6 + 0.048e6, _DRAM),
-    (4, "color", "list", 4): (3.102e9 + 192.306e9, _DRAM),
+    (5, "color", "count", 4): (30.719e6 + 0.040e6, _DRAM),
+    (4, "color", "list", 4): (3.352e9 + 192.248e9, _DRAM),
+    (4, "degree", "list", 4): (6.684e9 + 190.315e9, "profiles/k_sdegree_cta_rmat20.md"),
 }
 
 
