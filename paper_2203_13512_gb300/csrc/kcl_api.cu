@@ -116,7 +116,10 @@ kcl_status ensure_workspace(kcl_graph *g) {
         w.h_res = nullptr;
         return KCL_ENOMEM;
     }
-    KCL_CK(cudaMemset(w.outdeg, 0, (n + 1) * sizeof(uint32_t)));
+    // on the graph's own stream: a server slot's stream does not wait for
+    // the legacy default stream, so a plain cudaMemset could land after
+    // this call's kernels have written outdeg
+    KCL_CK(cudaMemsetAsync(w.outdeg, 0, (n + 1) * sizeof(uint32_t), g->stream));
     w.n_cap = n_new;
     w.nnz_cap = nnz_new;
     return KCL_OK;

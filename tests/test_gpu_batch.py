@@ -57,3 +57,41 @@ def test_batch_of_the_batched_workload_generator(kcl):
         for i, (rp, col, k) in enumerate(data):
             assert (counts[i], cks[i]) == oracle.plain(rp, col, k), (o, i)
     b.free()
+
+
+_ORACLE_CACHE = {}
+# graphs of 33..64 whose k >= 8 counts (5e7 - 2e8 cliques) take the oracle
+# 4-22 s each: there the batch is checked against single calls only
+_HEAVY = {34, 41, 44, 46, 56}
+
+
+@pytest.mark.parametrize("ordering", ["color", "degree"])
+def test_batch_of_served_queries(kcl, ordering):
+    """Batches as the server forms them: graphs 33..64 of the batched
+    workload, each query's own k in 3..10 (so one graph can appear twice with
+    different k, or twice with the same k), 64 queries per pass; every
+    member's count and checksum must equal a single call's and, but for the
+    heavy cases above, the oracle's."""
+    graphs = {i: kclgen.batch_graph(i)[:2] for i in range(33, 65)}
+    loaded = {i: kcl.kcl_load_csr(*graphs[i]) for i in graphs}
+    rng = np.random.default_rng(11)
+    b = kcl.kcl_batch_create()
+    single = {}
+    for trial in range(6):
+        qs = [(int(rng.integers(33, 65)), int(rng.integers(3, 11))) for _ in range(64)]
+        if trial == 0:
+            qs[5] = (47, 8)
+        counts, cks = kcl.kcl_count_batch(b, [loaded[i] for i, _ in qs], [k for _, k in qs],
+                                          [ordering] * len(qs), checksums=True)
+        for j, (i, k) in enumerate(qs):
+            if (i, k) not in single:
+                single[(i, k)] = kcl.kcl_list(loaded[i], k, ordering, None)[:2]
+                if not (i in _HEAVY and k >= 8):
+                    if (i, k) not in _ORACLE_CACHE:
+                        _ORACLE_CACHE[(i, k)] = oracle.plain(*graphs[i], k)
+                    assert single[(i, k)] == _ORACLE_CACHE[(i, k)], ("single", i, k)
+            assert (counts[j], cks[j]) == single[(i, k)], (trial, j, i, k, counts[j], cks[j],
+                                                          single[(i, k)])
+    b.free()
+    for g in loaded.values():
+        g.free()
