@@ -86,7 +86,8 @@ typedef struct {
 
 /* Copy a graph in and validate it (Section III-A problem input).
  * n: vertex count (0 allowed).  row_ptr/col: CSR as above, host memory if
- * on_device = 0, device memory of the current device if on_device = 1.
+ * on_device = 0, device memory of the current device if on_device = 1
+ * (read in order on `stream`, after the caller's earlier work there).
  * stream: cudaStream_t (void*) used for this graph from now on.
  * out: receives the new graph handle; NULL on error.
  * Returns KCL_EINVAL for a malformed graph, KCL_ENOMEM, KCL_ECUDA. */

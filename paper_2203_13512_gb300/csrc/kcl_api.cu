@@ -556,7 +556,10 @@ kcl_status kcl_load_csr(uint32_t n, const uint64_t *row_ptr, const uint32_t *col
         return fail(KCL_ECUDA);
     uint64_t nnz = 0;
     if (on_device) {
-        if (cudaMemcpy(&nnz, row_ptr + n, sizeof(uint64_t), cudaMemcpyDeviceToHost) != cudaSuccess)
+        // ordered on the graph's stream, after the caller's work there
+        if (cudaMemcpyAsync(&nnz, row_ptr + n, sizeof(uint64_t), cudaMemcpyDeviceToHost,
+                            g->stream) != cudaSuccess ||
+            cudaStreamSynchronize(g->stream) != cudaSuccess)
             return fail(KCL_ECUDA);
     } else {
         nnz = row_ptr[n];
