@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
+
 #include "../../include/kcl.h"
 
 namespace kcl {
@@ -458,19 +460,22 @@ __device__ __forceinline__ void hash_size(uint32_t d, uint32_t *T, uint32_t *shi
 // calls running concurrently on several host threads must not shrink it
 // under each other.
 inline int max_dynamic_smem() {
-    static int cached[64] = {0};
+    static std::atomic<int> cached[64];  // 0 = not yet read (several host threads call this)
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) {
         (void)cudaGetLastError();
         dev = 0;
     }
-    if (dev >= 0 && dev < 64 && cached[dev]) return cached[dev];
+    if (dev >= 0 && dev < 64) {
+        const int c = cached[dev].load(std::memory_order_relaxed);
+        if (c) return c;
+    }
     int v = 48 * 1024;
     if (cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) {
         (void)cudaGetLastError();
         v = 48 * 1024;
     }
-    if (dev >= 0 && dev < 64) cached[dev] = v;
+    if (dev >= 0 && dev < 64) cached[dev].store(v, std::memory_order_relaxed);
     return v;
 }
 

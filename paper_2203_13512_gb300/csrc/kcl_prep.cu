@@ -901,7 +901,8 @@ constexpr int kPeelThreads = 1024;
 // Blocks of the cooperative peel for n vertices: one per SM (fewer arrivals
 // per grid barrier), none beyond what n needs; -1 if it cannot be resident.
 int peel_blocks(int num_sms, uint32_t n) {
-    static int per_sm = -1;
+    static std::atomic<int> cached{-1};  // several host threads (server slots) call this
+    int per_sm = cached.load(std::memory_order_relaxed);
     if (per_sm < 0) {
         int b = 0;
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_peel_coop, kPeelThreads, 0) != cudaSuccess) {
@@ -909,6 +910,7 @@ int peel_blocks(int num_sms, uint32_t n) {
             b = 0;
         }
         per_sm = b;
+        cached.store(b, std::memory_order_relaxed);
     }
     if (per_sm <= 0) return -1;
     int blocks = num_sms;
