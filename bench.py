@@ -288,24 +288,41 @@ def run_ours(args, rank, world):
         # bounded samples of the batched and served forms (their own
         # --form lines run them at full size)
         bt = batch_form(args.summary_batch_graphs, quiet=True)
-        res["batched"] = {"graphs": bt["config"]["graphs"],
-                          "batched_graphs_per_s": bt["value"],
-                          "per_graph_graphs_per_s": bt["per_graph_value"],
-                          "speedup": bt["speedup"], "bit_exact": bt["bit_exact"],
-                          "sample": "graphs 0..%d of the batched workload, both orderings, "
-                                    "count + checksum" % (bt["config"]["graphs"] - 1)}
+        res["batched"] = batched_summary(bt)
         sv = serve_form(args.summary_serve_queries, [10000.0], args.serve_limit_ms,
                         rmat_ids=range(1, 9), batch_ids=range(33, 57), rmat_scale=lambda i: 16,
                         quiet=True)
-        r = sv["rates"]["10000.0"]
-        res["served"] = {"queries": sv["config"]["queries"], "rate_per_s": 10000.0,
-                         "time_limit_ms": args.serve_limit_ms,
-                         "served": r["served"], "fifo": r["fifo"],
-                         "results_compared_equal": sv["results_compared_equal"],
-                         "bit_exact": sv["bit_exact"],
-                         "sample": "8 R-MAT scale-16 graphs + batched-workload graphs 33..56, "
-                                   "k 3..10, Poisson arrivals at 10k/s"}
+        res["served"] = served_summary(sv, 10000.0, args.serve_limit_ms)
     return res
+
+
+def batched_summary(bt):
+    """The default line's record of a bounded batched-form run."""
+    out = {"graphs": bt["config"]["graphs"],
+           "batched_graphs_per_s": bt["value"],
+           "per_graph_graphs_per_s": bt["per_graph_value"],
+           "speedup": bt["speedup"], "bit_exact": bt["bit_exact"],
+           "sample": "graphs 0..%d of the batched workload, both orderings, "
+                     "count + checksum" % (bt["config"]["graphs"] - 1)}
+    if not bt["bit_exact"]:
+        out["mismatches"] = bt.get("mismatches")
+    return out
+
+
+def served_summary(sv, rate, limit_ms):
+    """The default line's record of a bounded served-form run at one rate."""
+    r = sv["rates"][str(float(rate))]
+    return {"queries": sv["config"]["queries"], "rate_per_s": rate,
+            "time_limit_ms": limit_ms,
+            "served": r["served"], "fifo": r["fifo"],
+            "results_compared": sv["results_compared"],
+            "results_compared_equal": sv["results_compared_equal"],
+            "bit_exact": sv["bit_exact"],
+            "mismatches": sv.get("mismatches"),
+            "sample": "%d R-MAT graphs (scales %s) + %d batched-workload graphs, k 3..10, "
+                      "Poisson arrivals at %g/s" % (sv["config"]["rmat_graphs"],
+                                                     sv["config"]["rmat_scales"],
+                                                     sv["config"]["batch_graphs"], rate)}
 
 
 def run_c1(golden, repeats=20):
@@ -672,6 +689,7 @@ def batch_form(G, quiet=False):
                       "generation_s": round(gen_s, 1)},
            "data": "synthetic (seeded Chung-Lu generator)", "orderings": {}}
     total_per, total_bat, cliques = 0.0, 0.0, 0
+    mismatches, mismatch_list = 0, []
     for o in ("color", "degree"):
         ords = [o] * G
 
@@ -686,7 +704,11 @@ def batch_form(G, quiet=False):
         if not quiet:
             print("batch %s: warm-up per-graph pass done" % o, file=sys.stderr, flush=True)
         got = batched()
-        assert got == ref, "batched results differ from per-graph results"
+        bad = [i for i, (x, y) in enumerate(zip(got, ref)) if x != y]
+        mismatches += len(bad)
+        for i in bad[:4]:
+            mismatch_list.append({"ordering": o, "graph": i, "batched": list(got[i]),
+                                  "alone": list(ref[i])})
         torch.cuda.synchronize()
         t = time.perf_counter()
         per_graph()
@@ -710,7 +732,10 @@ def batch_form(G, quiet=False):
     out["per_graph_value"] = 2 * G / total_per
     out["speedup"] = total_per / total_bat
     out["k_cliques_per_s_batched"] = cliques / total_bat
-    out["bit_exact"] = True
+    out["bit_exact"] = mismatches == 0
+    if mismatches:
+        out["mismatches"] = mismatches
+        out["mismatch_examples"] = mismatch_list
     b.free()
     for g in graphs:
         g.free()
@@ -774,7 +799,7 @@ def serve_form(Q, rates, limit, rmat_ids=range(1, 33), batch_ids=range(33, 65),
                       "k": "3..10", "slots": 8, "scratch_budget_gb": 100,
                       "time_limit_ms": limit, "load_s": round(load_s, 1)},
            "data": "synthetic", "rates": {}}
-    compared = 0
+    compared, mismatches, mismatch_list = 0, 0, []
     for rate in rates:
         arr = np.cumsum(gaps / rate)
         # FIFO: one query per call in arrival order, replayed against the clock
@@ -807,8 +832,13 @@ def serve_form(Q, rates, limit, rmat_ids=range(1, 33), batch_ids=range(33, 65),
             print("served at %g/s" % rate, file=sys.stderr, flush=True)
         for r, (c, h, st), q in zip(res, fifo_res, qs):
             if r["status"] == 0 and st == 0:
-                assert (r["count"], r["checksum"]) == (c, h), q
                 compared += 1
+                if (r["count"], r["checksum"]) != (c, h):
+                    mismatches += 1
+                    if len(mismatch_list) < 8:
+                        mismatch_list.append({"rate": rate, "query": list(q),
+                                              "served": [r["count"], r["checksum"]],
+                                              "fifo": [c, h]})
         ok_s = [r for r in res if r["status"] == 0]
         slat = [r["done_s"] - r["submit_s"] for r in ok_s]
         flat = [lt for lt, (_, _, st) in zip(fifo_lat, fifo_res) if st == 0]
@@ -827,8 +857,11 @@ def serve_form(Q, rates, limit, rmat_ids=range(1, 33), batch_ids=range(33, 65),
                      "p99_ms": 1e3 * float(np.percentile(flat, 99)) if flat else None}}
     last = out["rates"][str(rates[-1])]
     out["value"] = last["served"]["throughput_qps"]
-    out["results_compared_equal"] = compared
-    out["bit_exact"] = True
+    out["results_compared"] = compared
+    out["results_compared_equal"] = compared - mismatches
+    out["bit_exact"] = mismatches == 0
+    if mismatches:
+        out["mismatches"] = mismatch_list
     for g in graphs:
         g.free()
     return out

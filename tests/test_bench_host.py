@@ -119,3 +119,135 @@ def test_max_over_ranks_two_gloo_ranks():
 
 def test_max_over_ranks_single_rank():
     assert bench.max_over_ranks([3.0, 4.0], 1) == [3.0, 4.0]
+
+
+# ------------------------------------------ batched / served forms' host loop
+class _FakeGraph:
+    def __init__(self, key):
+        self.key = key
+
+    def free(self):
+        pass
+
+
+def _answer(key, k):
+    return (key * 1000 + k, (key * 7919 + 31 * k) & 0xFFFF)
+
+
+class _FakeLib:
+    """Stands in for the CUDA library so the forms' control flow (timing,
+    result comparison, report) runs on the CPU; results are a function of
+    (graph, k), and `wrong` names queries the fake server answers wrongly."""
+
+    class KclError(Exception):
+        def __init__(self, status):
+            super().__init__(status)
+            self.status = status
+
+    def __init__(self, wrong=()):
+        self.n = 0
+        self.wrong = set(wrong)
+
+    def kcl_load_csr(self, rp, col):
+        self.n += 1
+        return _FakeGraph(len(rp) * 100003 + len(col))
+
+    def kcl_set_time_limit(self, g, ms):
+        pass
+
+    def kcl_count(self, g, k, o):
+        return _answer(g.key, k)[0]
+
+    def kcl_list(self, g, k, o, ring, wrap=False):
+        c, h = _answer(g.key, k)
+        return c, h, 0, False
+
+    def kcl_batch_create(self):
+        return _FakeGraph(0)
+
+    def kcl_count_batch(self, b, gs, ks, ords, checksums=False):
+        res = [_answer(g.key, k) for g, k in zip(gs, ks)]
+        cks = [h for _, h in res] if checksums else None
+        counts = [c + (1 if (g.key, k) in self.wrong else 0) for (c, _), g, k in zip(res, gs, ks)]
+        return counts, cks
+
+    def kcl_server_create(self, slots, scratch_budget_bytes, small_nnz):
+        import time as _t
+        srv = _FakeGraph(0)
+        srv.t0, srv.graphs, srv.tickets = _t.perf_counter(), [], []
+        srv.destroy = lambda: None
+        return srv
+
+    def kcl_server_set_time_limit(self, srv, ms):
+        pass
+
+    def kcl_server_add_graph(self, srv, g):
+        srv.graphs.append(g)
+        return len(srv.graphs) - 1
+
+    def kcl_server_clock(self, srv):
+        import time as _t
+        return _t.perf_counter() - srv.t0
+
+    def kcl_server_submit(self, srv, gid, k, o, lst=False):
+        srv.tickets.append((gid, k, lst, self.kcl_server_clock(srv)))
+        return len(srv.tickets) - 1
+
+    def kcl_server_wait(self, srv, t):
+        gid, k, lst, sub = srv.tickets[t]
+        g = srv.graphs[gid]
+        c, h = _answer(g.key, k)
+        if (g.key, k) in self.wrong:
+            c += 1
+        now = self.kcl_server_clock(srv)
+        return {"status": 0, "count": c, "checksum": h if lst else 0, "submit_s": sub,
+                "start_s": sub, "done_s": max(now, sub + 1e-6), "batch": 1}
+
+
+def _use_fake(monkeypatch, lib):
+    import sys
+    import types
+
+    import torch
+    mod = types.ModuleType("paper_2203_13512_gb300")
+    for name in dir(lib):
+        if not name.startswith("__"):
+            setattr(mod, name, getattr(lib, name))
+    monkeypatch.setitem(sys.modules, "paper_2203_13512_gb300", mod)
+    monkeypatch.setattr(torch.cuda, "synchronize", lambda *a, **k: None)
+
+
+def test_batch_form_reports_mismatches(monkeypatch):
+    import kclgen
+    _use_fake(monkeypatch, _FakeLib())
+    out = bench.batch_form(4, quiet=True)
+    assert out["bit_exact"] and out["config"]["graphs"] == 4 and out["speedup"] > 0
+    summ = bench.batched_summary(out)
+    assert summ["graphs"] == 4 and summ["bit_exact"] and "mismatches" not in summ
+    rp, col, _ = kclgen.batch_graph(2)
+    key = len(rp) * 100003 + len(col)
+    k = kclgen.batch_graph(2)[2]
+    _use_fake(monkeypatch, _FakeLib(wrong={(key, k)}))
+    out = bench.batch_form(4, quiet=True)
+    assert not out["bit_exact"] and out["mismatches"] == 2  # both orderings
+    assert out["mismatch_examples"][0]["graph"] == 2
+    assert bench.batched_summary(out)["mismatches"] == 2
+
+
+def test_serve_form_compares_and_reports(monkeypatch):
+    kw = dict(rmat_ids=range(1, 3), batch_ids=range(33, 35), rmat_scale=lambda i: 8, quiet=True)
+    _use_fake(monkeypatch, _FakeLib())
+    out = bench.serve_form(24, [1e5], 50, **kw)
+    r = out["rates"]["100000.0"]
+    assert out["bit_exact"] and out["results_compared"] == 24
+    assert out["results_compared_equal"] == 24 and r["served"]["completed"] == 24
+    summ = bench.served_summary(out, 1e5, 50)
+    assert summ["bit_exact"] and summ["results_compared"] == 24 and summ["mismatches"] is None
+    assert "2 R-MAT graphs (scales 8..8) + 2 batched-workload graphs" in summ["sample"]
+    import kclgen
+    rp, col = kclgen.rmat20(seed=1, scale=8)
+    _use_fake(monkeypatch, _FakeLib(wrong={(len(rp) * 100003 + len(col), k) for k in range(3, 11)}))
+    out = bench.serve_form(24, [1e5], 50, **kw)
+    assert not out["bit_exact"] and out["mismatches"]
+    assert out["results_compared_equal"] < out["results_compared"] == 24
+    assert not bench.served_summary(out, 1e5, 50)["bit_exact"]
