@@ -1012,7 +1012,8 @@ def main():
     ap.add_argument("--serve-queries", type=int, default=5000)
     ap.add_argument("--serve-rates", type=float, nargs="+", default=[1000.0, 10000.0, 50000.0])
     ap.add_argument("--serve-limit-ms", type=int, default=50,
-                    help="time limit of every pass of the served form, both sides")
+                    help="time limit per query of the served form: each FIFO call gets it, a "
+                         "batched pass of n queries gets n times it")
     ap.add_argument("--profile-case", default=None,
                     help="SCALE:K:ORDERING[:count|list] -- one call on R-MAT at SCALE "
                          "(16 * 2^SCALE edges, seed 1), for profilers")
